@@ -1,0 +1,204 @@
+/*
+ * tgv.h - C ABI of the B300 (sm_103a) Taylor-Green-vortex hot path.
+ *
+ * The library advances the compressible Navier-Stokes equations on a periodic
+ * N^3 grid with explicit 4th-order central differences (arXiv 2505.20911,
+ * Sec. 2.3.1) and the low-storage 3-stage Runge-Kutta scheme of Sec. 3.1,
+ * Eqs. 3-5, starting from the Taylor-Green field of Sec. 4.1, Eqs. 6-10.
+ *
+ * Conventions shared by every entry point
+ *  - Layout: a state Q is 5 planar fields (rho, rho*u, rho*v, rho*w, rho*E),
+ *    each N^3 contiguous elements, x fastest: element (c, k, j, i) lives at
+ *    offset (c*N + k)*N*N + j*N + i  (c field, k = z, j = y, i = x index),
+ *    grid point x_i = i*L/N.  Qt (the Runge-Kutta increment) has the same
+ *    layout.  Element types are given by the config (tgv_dtype).
+ *  - Ownership: the caller allocates every buffer (device memory unless the
+ *    name says host) and keeps ownership.  Apart from the ensemble handle
+ *    (tgv_ensemble_create / tgv_ensemble_destroy), the library allocates no
+ *    memory; scratch space is a caller-provided device workspace whose size a
+ *    *_workspace_bytes query returns.
+ *  - Streams: `stream` is a cudaStream_t (NULL = legacy default stream).
+ *    Work is enqueued on it; functions return without synchronising unless
+ *    stated.  Buffers must not be touched by other streams meanwhile.
+ *  - Errors: every function returns a tgv_status.  Arguments are validated on
+ *    the host before any CUDA call; a failing CUDA call maps to TGV_ERR_CUDA.
+ *    Nothing aborts, traps on the device, or prints.
+ *  - Encoding (reading of Sec. 4.2's failure of pure FP16 storage): with
+ *    TGV_ENC_OFFSET, stored rho and rho*E are the deviations from the uniform
+ *    base state rho0 = 1 and (rho E)0 = 1/(gamma (gamma-1) M^2); kernels add the
+ *    offsets back in the compute type.  TGV_ENC_PLAIN stores the plain values.
+ */
+#ifndef TGV_H_
+#define TGV_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define TGV_ABI_VERSION 1
+#define TGV_DIAG_COUNT 10
+
+typedef enum { TGV_F64 = 0, TGV_F32 = 1, TGV_BF16 = 2, TGV_F16 = 3 } tgv_dtype;
+
+typedef enum {
+  TGV_OK = 0,
+  TGV_ERR_ARG = -1,          /* invalid argument (null pointer, bad size)      */
+  TGV_ERR_UNSUPPORTED = -2,  /* valid but not built (precision combination)    */
+  TGV_ERR_CUDA = -3,         /* a CUDA runtime call failed                     */
+  TGV_ERR_NONFINITE = -4,    /* a diagnostic found NaN/Inf in the state        */
+  TGV_ERR_UNSTABLE_DT = -5,  /* dt above the acoustic stability limit          */
+  TGV_ERR_TIMEOUT = -6,      /* a bounded device wait ran out                  */
+  TGV_ERR_WORKSPACE = -7     /* workspace null or smaller than required        */
+} tgv_status;
+
+typedef enum { TGV_SPLIT_BLAISDELL = 0, TGV_SPLIT_DIVERGENCE = 1 } tgv_split;
+typedef enum { TGV_ENC_PLAIN = 0, TGV_ENC_OFFSET = 1 } tgv_encoding;
+
+/* Flags of tgv_config.flags */
+#define TGV_FLAG_ALLOW_UNSTABLE_DT 1  /* skip the dt stability check            */
+
+/*
+ * One TGV problem.  Physics follows Sec. 3.1 / Sec. 4.1 (nondimensional):
+ * p = (gamma-1)(rho E - rho|u|^2/2), T = gamma M^2 p / rho,
+ * tau_ij = (mu/Re)(du_i/dx_j + du_j/dx_i - 2/3 delta_ij div u),
+ * q_j = -mu/((gamma-1) M^2 Pr Re) dT/dx_j.  mu = 0 gives the inviscid limit.
+ *
+ * Precision (Sec. 3.1 storage of Q / Qt and the precision of R and W): Q is
+ * stored as q_storage, Qt as qt_storage, the residual is computed in
+ * `compute`, the RK axpy of Eqs. 3-4 in `accumulate`.  Built combinations
+ * (q_storage, qt_storage, compute, accumulate):
+ *   F64 F64 F64 F64  double                 F64 F64 F32 F64  single-double (Q FP64)
+ *   F32 F32 F64 F64  FP32 storage/FP64 comp F32 F32 F32 F32  single
+ *   BF16 BF16 F32 F32 bf16-single           F16 F16 F32 F32  half-single
+ *   F16 F16 F16 F32  pure half              F32 F16 F32 F32  Q FP32 / Qt FP16
+ * Anything else returns TGV_ERR_UNSUPPORTED.
+ */
+typedef struct tgv_config {
+  int32_t n;          /* N: grid points per direction, 8..1024 (any value) */
+  int32_t split_form; /* tgv_split                                            */
+  int32_t q_storage;  /* tgv_dtype of Q                                       */
+  int32_t qt_storage; /* tgv_dtype of Qt                                      */
+  int32_t compute;    /* tgv_dtype of the residual arithmetic (F64/F32/F16)   */
+  int32_t accumulate; /* tgv_dtype of the RK update arithmetic (F64/F32)      */
+  int32_t encoding;   /* tgv_encoding                                         */
+  int32_t tile;       /* stencil tile id, 0 = default (see tgv_tile_count)    */
+  int32_t zchunk;     /* z planes per thread block, 0 = chosen by the library */
+  int32_t flags;      /* TGV_FLAG_*                                           */
+  double length;      /* periodic box edge L (2*pi for the TGV)               */
+  double gamma;       /* ratio of specific heats (1.4)                        */
+  double mach;        /* reference Mach number M                              */
+  double re;          /* Reynolds number                                      */
+  double pr;          /* Prandtl number (0.71)                                */
+  double mu;          /* constant nondimensional viscosity (1, or 0: inviscid) */
+} tgv_config;
+
+/* ABI version (TGV_ABI_VERSION) and a static message for a status code. */
+int32_t tgv_abi_version(void);
+const char* tgv_strerror(int32_t status);
+
+/* Host-only validation of a config: TGV_OK, TGV_ERR_ARG or TGV_ERR_UNSUPPORTED. */
+int32_t tgv_check_config(const tgv_config* cfg);
+
+/* Bytes of one Q (5*N^3*sizeof(q_storage)) and one Qt; 0 if cfg is invalid. */
+size_t tgv_state_bytes(const tgv_config* cfg);
+size_t tgv_qt_bytes(const tgv_config* cfg);
+
+/* Number of stencil tile shapes built, and the shape of tile id t (1-based). */
+int32_t tgv_tile_count(void);
+int32_t tgv_tile_shape(int32_t t, int32_t* tx, int32_t* ty);
+
+/*
+ * Largest stable time step (host only).  Reading of the paper's time-step
+ * choice (Sec. 4.2, heat-map study): the RK3 stability boundary on the
+ * imaginary axis, sqrt(3), divided by the largest modified acoustic wave
+ * speed of the 4th-order central difference, 1.3722/h * (sqrt(3)/M + |u|max),
+ * with |u|max = 1 for the TGV.  Returns 0 for an invalid config.
+ */
+double tgv_dt_max(const tgv_config* cfg);
+
+/*
+ * Taylor-Green initial condition (Sec. 4.1, Eqs. 6-10) into q (device, Q
+ * layout, q_storage, encoded).  Evaluated in FP64 on the device, then rounded.
+ */
+int32_t tgv_init(const tgv_config* cfg, void* q, void* stream);
+
+/*
+ * Residual R(Q) = dQ/dt of Sec. 3.1 (the "remaining terms" of the governing
+ * equations): Blaisdell-split convective terms (Sec. 2.3.1), pressure terms,
+ * viscous stress and heat flux, all 4th-order central.
+ * q: device, Q layout, q_storage.  r: device, Q layout, 5 fields of the
+ * compute type (not encoded).  Same stencil kernel as rk_step, with the
+ * residual written out instead of the RK update.
+ */
+int32_t rhs_eval(const tgv_config* cfg, const void* q, void* r, void* stream);
+
+/*
+ * Advance nsteps full RK3 steps (3 fused stage kernels each, Sec. 3.1,
+ * Eqs. 3-5; Williamson's 2N coefficients A = (0, -5/9, -153/128),
+ * B = (1/3, 15/16, 8/15)).
+ * q_a: device, holds Q^n on entry.  q_b: device, same size, scratch.  Stages
+ *   ping-pong between the two buffers (Q is never updated in place because
+ *   neighbouring blocks still read its halo); *parity_out (nullable) is set to
+ *   the buffer holding Q^(n+nsteps): 0 = q_a, 1 = q_b (that is, nsteps % 2).
+ * qt: device, Qt layout, qt_storage; its contents on entry are ignored
+ *   (A_1 = 0) and are garbage on return.
+ * diag_every > 0: diagnostics (as diagnostics_reduce) of Q^(n+m) for every m
+ *   in [0, nsteps] with m % diag_every == 0 are written to diag_dev
+ *   (device, double[(nsteps/diag_every + 1) * TGV_DIAG_COUNT]) in order.
+ *   diag_every = 0: diag_dev is not touched (may be NULL).
+ * workspace: device scratch of tgv_workspace_bytes(cfg) bytes (nullable
+ *   when diag_every = 0).
+ * Returns TGV_ERR_UNSTABLE_DT if dt > tgv_dt_max(cfg) and the flag
+ * TGV_FLAG_ALLOW_UNSTABLE_DT is not set.
+ */
+int32_t rk_step(const tgv_config* cfg, void* q_a, void* q_b, void* qt, double dt,
+                int32_t nsteps, int32_t diag_every, double* diag_dev,
+                void* workspace, size_t ws_bytes, int32_t* parity_out, void* stream);
+
+/*
+ * One RK substep i in {0,1,2} (Sec. 3.1, Eqs. 3-4) from q_in to q_out:
+ * Qt <- A_i Qt + dt R(q_in); q_out <- q_in + B_i Qt.  q_in and q_out must
+ * differ.  For i = 0 the incoming Qt is ignored.
+ */
+int32_t rk_substep(const tgv_config* cfg, const void* q_in, void* q_out, void* qt,
+                   int32_t i, double dt, void* stream);
+
+/* Device scratch needed by rk_step (with diagnostics) and diagnostics_reduce. */
+size_t tgv_workspace_bytes(const tgv_config* cfg);
+
+/*
+ * Diagnostics of Sec. 4.1, Eqs. 11-12, reduced in FP64 (reading: eps^S as a
+ * volume average, like K).  out_dev (device, double[TGV_DIAG_COUNT]):
+ *   [0] K = <|u|^2/2>        [1] <rho |u|^2/2>      [2] <omega.omega>
+ *   [3] eps^S = <omega.omega>/Re                     [4] <rho>
+ *   [5] <rho u>  [6] <rho v>  [7] <rho w>  [8] <rho E>
+ *   [9] number of grid points where any component of Q is NaN or Inf.
+ * <.> is the mean over the N^3 grid points; omega uses the 4th-order D.
+ * Deterministic: per-block FP64 partials, then a fixed-order second pass.
+ */
+int32_t diagnostics_reduce(const tgv_config* cfg, const void* q, double* out_dev,
+                           void* workspace, size_t ws_bytes, void* stream);
+
+/*
+ * End-to-end call with HOST buffers: copies q_host_in (Q layout, q_storage,
+ * encoded) to the device, advances nsteps RK3 steps with diagnostics every
+ * diag_every steps, copies Q^(n+nsteps) to q_host_out and the diagnostics
+ * ((nsteps/diag_every + 1) * TGV_DIAG_COUNT doubles) to diag_host (nullable),
+ * and synchronises the stream.  Device memory (two Q buffers, Qt, the
+ * diagnostics scratch and records) comes from dev_workspace, of at least
+ * tgv_run_host_workspace_bytes(cfg, nsteps, diag_every) bytes (0 = invalid).
+ * Pinned host memory is fastest.
+ */
+size_t tgv_run_host_workspace_bytes(const tgv_config* cfg, int32_t nsteps, int32_t diag_every);
+int32_t tgv_run_host(const tgv_config* cfg, const void* q_host_in, void* q_host_out,
+                     double dt, int32_t nsteps, int32_t diag_every, double* diag_host,
+                     void* dev_workspace, size_t ws_bytes, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* TGV_H_ */

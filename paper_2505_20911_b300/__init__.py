@@ -1,0 +1,204 @@
+"""B300-native Taylor-Green-vortex hot path (arXiv 2505.20911).
+
+The fused explicit finite-difference residual of the 3-D compressible
+Navier-Stokes equations and the low-storage RK3 update it feeds, as CUDA
+kernels for sm_103a behind a C ABI (include/tgv.h).  This module is the thin
+Python binding: it marshals torch tensors (device memory) and CUDA streams
+into the C calls, with the same names.  PyTorch provides memory and streams
+only; every step of the path runs in libtgv.so.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import math
+from dataclasses import dataclass, replace
+
+import torch
+
+from . import _abi
+from ._abi import (TGV_BF16, TGV_DIAG_COUNT, TGV_ENC_OFFSET, TGV_ENC_PLAIN, TGV_F16,  # noqa: F401
+                   TGV_F32, TGV_F64, TGV_FLAG_ALLOW_UNSTABLE_DT, TGV_SPLIT_BLAISDELL,
+                   TGV_SPLIT_DIVERGENCE, TGVError, check, lib)
+
+DIAG_NAMES = ("K", "K_rho", "enstrophy", "eps_S", "rho", "rho_u", "rho_v", "rho_w",
+              "rho_E", "nonfinite")
+
+TORCH_DTYPE = {TGV_F64: torch.float64, TGV_F32: torch.float32, TGV_BF16: torch.bfloat16,
+               TGV_F16: torch.float16}
+
+# Named precision modes: (q_storage, qt_storage, compute, accumulate).
+MODES = {
+    "fp64": (TGV_F64, TGV_F64, TGV_F64, TGV_F64),          # double
+    "spdp": (TGV_F64, TGV_F64, TGV_F32, TGV_F64),          # single-double: Q FP64, R FP32
+    "fp32s_fp64c": (TGV_F32, TGV_F32, TGV_F64, TGV_F64),   # FP32 storage / FP64 compute
+    "fp32": (TGV_F32, TGV_F32, TGV_F32, TGV_F32),          # single
+    "bf16_fp32": (TGV_BF16, TGV_BF16, TGV_F32, TGV_F32),   # bf16 storage / FP32 compute
+    "fp16_fp32": (TGV_F16, TGV_F16, TGV_F32, TGV_F32),     # half-single
+    "fp16": (TGV_F16, TGV_F16, TGV_F16, TGV_F32),          # pure half
+    "hpsp": (TGV_F32, TGV_F16, TGV_F32, TGV_F32),          # Q FP32, Qt FP16
+}
+
+
+@dataclass(frozen=True)
+class Config:
+    """Python mirror of tgv_config (include/tgv.h)."""
+
+    n: int
+    mode: str = "fp64"
+    mach: float = 0.1
+    re: float = 1600.0
+    pr: float = 0.71
+    gamma: float = 1.4
+    mu: float = 1.0
+    split: str = "blaisdell"
+    encoding: str = "plain"
+    tile: int = 0
+    zchunk: int = 0
+    allow_unstable_dt: bool = False
+    length: float = 2.0 * math.pi
+
+    def with_(self, **kw) -> "Config":
+        return replace(self, **kw)
+
+    @property
+    def q_dtype(self) -> torch.dtype:
+        return TORCH_DTYPE[MODES[self.mode][0]]
+
+    @property
+    def qt_dtype(self) -> torch.dtype:
+        return TORCH_DTYPE[MODES[self.mode][1]]
+
+    @property
+    def compute_dtype(self) -> torch.dtype:
+        return TORCH_DTYPE[MODES[self.mode][2]]
+
+    def c(self) -> _abi.tgv_config:
+        qs, qts, comp, acc = MODES[self.mode]
+        return _abi.tgv_config(
+            n=self.n,
+            split_form={"blaisdell": TGV_SPLIT_BLAISDELL, "divergence": TGV_SPLIT_DIVERGENCE}[self.split],
+            q_storage=qs, qt_storage=qts, compute=comp, accumulate=acc,
+            encoding={"plain": TGV_ENC_PLAIN, "offset": TGV_ENC_OFFSET}[self.encoding],
+            tile=self.tile, zchunk=self.zchunk,
+            flags=TGV_FLAG_ALLOW_UNSTABLE_DT if self.allow_unstable_dt else 0,
+            length=self.length, gamma=self.gamma, mach=self.mach, re=self.re, pr=self.pr,
+            mu=self.mu)
+
+
+def _ptr(t) -> int | None:
+    if t is None:
+        return None
+    if not t.is_cuda:
+        raise ValueError("expected a CUDA tensor")
+    if not t.is_contiguous():
+        raise ValueError("expected a contiguous tensor")
+    return t.data_ptr()
+
+
+def _stream(stream) -> int | None:
+    if stream is None:
+        return torch.cuda.current_stream().cuda_stream
+    return stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)
+
+
+# ------------------------------------------------------------------ host-only
+def tgv_check_config(cfg: Config) -> int:
+    return lib().tgv_check_config(C.byref(cfg.c()))
+
+
+def tgv_state_bytes(cfg: Config) -> int:
+    return lib().tgv_state_bytes(C.byref(cfg.c()))
+
+
+def tgv_qt_bytes(cfg: Config) -> int:
+    return lib().tgv_qt_bytes(C.byref(cfg.c()))
+
+
+def tgv_dt_max(cfg: Config) -> float:
+    return lib().tgv_dt_max(C.byref(cfg.c()))
+
+
+def tgv_workspace_bytes(cfg: Config) -> int:
+    return lib().tgv_workspace_bytes(C.byref(cfg.c()))
+
+
+def tgv_tile_shapes() -> list[tuple[int, int]]:
+    out = []
+    for t in range(1, lib().tgv_tile_count() + 1):
+        tx, ty = C.c_int32(), C.c_int32()
+        check(lib().tgv_tile_shape(t, C.byref(tx), C.byref(ty)), "tgv_tile_shape")
+        out.append((tx.value, ty.value))
+    return out
+
+
+# ------------------------------------------------------------ allocation help
+def empty_state(cfg: Config, device="cuda") -> torch.Tensor:
+    """A (5, N, N, N) tensor of the Q storage type."""
+    return torch.empty((5, cfg.n, cfg.n, cfg.n), dtype=cfg.q_dtype, device=device)
+
+
+def empty_qt(cfg: Config, device="cuda") -> torch.Tensor:
+    return torch.empty((5, cfg.n, cfg.n, cfg.n), dtype=cfg.qt_dtype, device=device)
+
+
+def empty_workspace(cfg: Config, device="cuda") -> torch.Tensor:
+    return torch.empty(max(tgv_workspace_bytes(cfg), 8), dtype=torch.uint8, device=device)
+
+
+# ------------------------------------------------------------------ C entries
+def tgv_init(cfg: Config, q: torch.Tensor, stream=None) -> None:
+    check(lib().tgv_init(C.byref(cfg.c()), _ptr(q), _stream(stream)), "tgv_init")
+
+
+def rhs_eval(cfg: Config, q: torch.Tensor, r: torch.Tensor, stream=None) -> None:
+    if r.dtype != cfg.compute_dtype:
+        raise ValueError(f"r must be {cfg.compute_dtype}")
+    check(lib().rhs_eval(C.byref(cfg.c()), _ptr(q), _ptr(r), _stream(stream)), "rhs_eval")
+
+
+def rk_substep(cfg: Config, q_in, q_out, qt, i: int, dt: float, stream=None) -> None:
+    check(lib().rk_substep(C.byref(cfg.c()), _ptr(q_in), _ptr(q_out), _ptr(qt), int(i),
+                           float(dt), _stream(stream)), "rk_substep")
+
+
+def rk_step(cfg: Config, q_a, q_b, qt, dt: float, nsteps: int, diag_every: int = 0,
+            diag=None, workspace=None, stream=None) -> int:
+    """Advance nsteps; returns the parity (0: result in q_a, 1: in q_b)."""
+    par = C.c_int32(-1)
+    ws = workspace
+    ws_bytes = ws.numel() * ws.element_size() if ws is not None else 0
+    check(lib().rk_step(C.byref(cfg.c()), _ptr(q_a), _ptr(q_b), _ptr(qt), float(dt),
+                        int(nsteps), int(diag_every), _ptr(diag), _ptr(ws), ws_bytes,
+                        C.byref(par), _stream(stream)), "rk_step")
+    return par.value
+
+
+def diagnostics_reduce(cfg: Config, q, out, workspace, stream=None) -> None:
+    check(lib().diagnostics_reduce(C.byref(cfg.c()), _ptr(q), _ptr(out), _ptr(workspace),
+                                   workspace.numel() * workspace.element_size(),
+                                   _stream(stream)), "diagnostics_reduce")
+
+
+def tgv_run_host_workspace_bytes(cfg: Config, nsteps: int, diag_every: int) -> int:
+    return lib().tgv_run_host_workspace_bytes(C.byref(cfg.c()), int(nsteps), int(diag_every))
+
+
+def tgv_run_host(cfg: Config, q_host_in, q_host_out, dt: float, nsteps: int,
+                 diag_every: int = 0, diag_host=None, dev_workspace=None, stream=None) -> None:
+    """End-to-end call with host (CPU, ideally pinned) tensors."""
+    for t in (q_host_in, q_host_out) + ((diag_host,) if diag_host is not None else ()):
+        if t.is_cuda or not t.is_contiguous():
+            raise ValueError("host buffers must be contiguous CPU tensors")
+    ws_bytes = dev_workspace.numel() * dev_workspace.element_size()
+    check(lib().tgv_run_host(C.byref(cfg.c()), q_host_in.data_ptr(), q_host_out.data_ptr(),
+                             float(dt), int(nsteps), int(diag_every),
+                             diag_host.data_ptr() if diag_host is not None else None,
+                             _ptr(dev_workspace), ws_bytes, _stream(stream)), "tgv_run_host")
+
+
+def diagnostics(cfg: Config, q: torch.Tensor, workspace=None) -> dict:
+    """Convenience: diagnostics_reduce into a fresh tensor, returned as a dict."""
+    ws = workspace if workspace is not None else empty_workspace(cfg, q.device)
+    out = torch.empty(TGV_DIAG_COUNT, dtype=torch.float64, device=q.device)
+    diagnostics_reduce(cfg, q, out, ws)
+    return dict(zip(DIAG_NAMES, out.cpu().tolist()))

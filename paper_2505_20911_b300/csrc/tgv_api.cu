@@ -1,0 +1,374 @@
+// tgv_api.cu - the C ABI declared in include/tgv.h.
+//
+// Host-side validation, mode dispatch, z-chunk selection and the RK3 driver
+// loop (three fused stage launches per step, buffers ping-ponged).
+#include <cmath>
+#include <cstring>
+#include <atomic>
+
+#include "tgv_modes.cuh"
+
+namespace tgv {
+
+const ModeLaunchers& mode_launchers_0();
+const ModeLaunchers& mode_launchers_1();
+const ModeLaunchers& mode_launchers_2();
+const ModeLaunchers& mode_launchers_3();
+const ModeLaunchers& mode_launchers_4();
+const ModeLaunchers& mode_launchers_5();
+const ModeLaunchers& mode_launchers_6();
+const ModeLaunchers& mode_launchers_7();
+
+const ModeLaunchers& mode_launchers(int m) {
+  switch (m) {
+    case 0: return mode_launchers_0();
+    case 1: return mode_launchers_1();
+    case 2: return mode_launchers_2();
+    case 3: return mode_launchers_3();
+    case 4: return mode_launchers_4();
+    case 5: return mode_launchers_5();
+    case 6: return mode_launchers_6();
+    default: return mode_launchers_7();
+  }
+}
+
+Problem make_problem(const tgv_config& c) {
+  Problem P;
+  P.n = c.n;
+  P.split = c.split_form;
+  P.encoding = c.encoding;
+  P.h = c.length / c.n;
+  P.inv12h = 1.0 / (12.0 * P.h);
+  P.inv12h2 = 1.0 / (12.0 * P.h * P.h);
+  P.gamma = c.gamma;
+  P.gm1 = c.gamma - 1.0;
+  P.gM2 = c.gamma * c.mach * c.mach;
+  P.nu = c.mu / c.re;
+  P.kappa = c.mu / ((c.gamma - 1.0) * c.mach * c.mach * c.pr * c.re);
+  if (c.encoding == TGV_ENC_OFFSET) {
+    P.rho0 = 1.0;
+    P.rhoE0 = 1.0 / (c.gamma * (c.gamma - 1.0) * c.mach * c.mach);
+  } else {
+    P.rho0 = 0.0;
+    P.rhoE0 = 0.0;
+  }
+  P.mach = c.mach;
+  P.re = c.re;
+  return P;
+}
+
+static int find_mode(const tgv_config& c) {
+  for (int m = 0; m < NUM_MODES; ++m) {
+    const ModeKey& k = MODE_KEYS[m];
+    if (k.qs == c.q_storage && k.qts == c.qt_storage && k.comp == c.compute && k.acc == c.accumulate)
+      return m;
+  }
+  return -1;
+}
+
+static bool valid_dtype(int d) { return d >= TGV_F64 && d <= TGV_F16; }
+
+static int32_t check(const tgv_config* c) {
+  if (!c) return TGV_ERR_ARG;
+  if (c->n < 8 || c->n > 1024) return TGV_ERR_ARG;
+  if (c->split_form != TGV_SPLIT_BLAISDELL && c->split_form != TGV_SPLIT_DIVERGENCE) return TGV_ERR_ARG;
+  if (!valid_dtype(c->q_storage) || !valid_dtype(c->qt_storage) || !valid_dtype(c->compute) ||
+      !valid_dtype(c->accumulate))
+    return TGV_ERR_ARG;
+  if (c->encoding != TGV_ENC_PLAIN && c->encoding != TGV_ENC_OFFSET) return TGV_ERR_ARG;
+  if (c->tile < 0 || c->tile > NUM_TILES) return TGV_ERR_ARG;
+  if (c->zchunk < 0 || c->zchunk > c->n) return TGV_ERR_ARG;
+  if (!(c->length > 0.0) || !(c->gamma > 1.0) || !(c->mach > 0.0) || !(c->re > 0.0) ||
+      !(c->pr > 0.0) || !(c->mu >= 0.0) || !std::isfinite(c->length) || !std::isfinite(c->re) ||
+      !std::isfinite(c->mu))
+    return TGV_ERR_ARG;
+  if (find_mode(*c) < 0) return TGV_ERR_UNSUPPORTED;
+  return TGV_OK;
+}
+
+// Default tile per mode: 32x8 when N fills it, else 16x8.
+static int pick_tile(const tgv_config& c) {
+  if (c.tile > 0) return c.tile - 1;
+  if (c.n % 32 == 0) return 0;
+  return 2;
+}
+
+// Per-device caches (SM count; resident CTAs per SM of each stage kernel).
+constexpr int MAX_DEVICES = 64;
+static std::atomic<int> g_sms[MAX_DEVICES];
+static std::atomic<int> g_occ[MAX_DEVICES][NUM_MODES][NUM_TILES];
+
+static int current_device() {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= MAX_DEVICES) return -1;
+  return dev;
+}
+
+static int device_sms(int dev) {
+  int v = g_sms[dev].load(std::memory_order_relaxed);
+  if (v > 0) return v;
+  if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
+  g_sms[dev].store(v, std::memory_order_relaxed);
+  return v;
+}
+
+static int stage_occ(int dev, int mode, int tile) {
+  int v = g_occ[dev][mode][tile].load(std::memory_order_relaxed);
+  if (v > 0) return v;
+  v = mode_launchers(mode).occupancy[tile]();
+  if (v > 0) g_occ[dev][mode][tile].store(v, std::memory_order_relaxed);
+  return v;
+}
+
+// z planes per CTA: balance whole waves of resident CTAs against the 4 extra
+// halo planes each chunk reads.
+static int pick_zchunk(const tgv_config& c, int tile, int occupancy, int sms) {
+  if (c.zchunk > 0) return c.zchunk;
+  const int n = c.n;
+  const int tx = TILE_TX[tile], ty = TILE_TY[tile];
+  const long long tiles = (long long)((n + tx - 1) / tx) * ((n + ty - 1) / ty);
+  const long long conc = (long long)(occupancy > 0 ? occupancy : 1) * (sms > 0 ? sms : 148);
+  double best = -1.0;
+  int best_zc = n;
+  for (int chunks = 1; chunks <= n / 8; ++chunks) {
+    const int zc = (n + chunks - 1) / chunks;
+    const long long ctas = tiles * ((n + zc - 1) / zc);
+    const long long waves = (ctas + conc - 1) / conc;
+    const double fill = (double)ctas / (double)(waves * conc);
+    const double eff = fill * (double)zc / (double)(zc + 4);
+    if (eff > best + 1e-9) { best = eff; best_zc = zc; }
+  }
+  return best_zc;
+}
+
+}  // namespace tgv
+
+using namespace tgv;
+
+extern "C" {
+
+int32_t tgv_abi_version(void) { return TGV_ABI_VERSION; }
+
+const char* tgv_strerror(int32_t s) {
+  switch (s) {
+    case TGV_OK: return "ok";
+    case TGV_ERR_ARG: return "invalid argument";
+    case TGV_ERR_UNSUPPORTED: return "unsupported precision combination";
+    case TGV_ERR_CUDA: return "CUDA runtime error";
+    case TGV_ERR_NONFINITE: return "non-finite value in the state";
+    case TGV_ERR_UNSTABLE_DT: return "dt above the stability limit";
+    case TGV_ERR_TIMEOUT: return "bounded device wait timed out";
+    case TGV_ERR_WORKSPACE: return "workspace missing or too small";
+  }
+  return "unknown status";
+}
+
+int32_t tgv_check_config(const tgv_config* cfg) { return check(cfg); }
+
+size_t tgv_state_bytes(const tgv_config* cfg) {
+  if (check(cfg) != TGV_OK) return 0;
+  const size_t n = (size_t)cfg->n;
+  return 5 * n * n * n * dtype_size(cfg->q_storage);
+}
+
+size_t tgv_qt_bytes(const tgv_config* cfg) {
+  if (check(cfg) != TGV_OK) return 0;
+  const size_t n = (size_t)cfg->n;
+  return 5 * n * n * n * dtype_size(cfg->qt_storage);
+}
+
+int32_t tgv_tile_count(void) { return NUM_TILES; }
+
+int32_t tgv_tile_shape(int32_t t, int32_t* tx, int32_t* ty) {
+  if (t < 1 || t > NUM_TILES || !tx || !ty) return TGV_ERR_ARG;
+  *tx = TILE_TX[t - 1];
+  *ty = TILE_TY[t - 1];
+  return TGV_OK;
+}
+
+double tgv_dt_max(const tgv_config* cfg) {
+  if (check(cfg) != TGV_OK) return 0.0;
+  const double h = cfg->length / cfg->n;
+  const double kmax = 1.3722 / h;  // max of (8 sin t - sin 2t)/(6h)
+  const double lam = kmax * (std::sqrt(3.0) / cfg->mach + 1.0);
+  return std::sqrt(3.0) / lam;
+}
+
+size_t tgv_workspace_bytes(const tgv_config* cfg) {
+  if (check(cfg) != TGV_OK) return 0;
+  return (size_t)DIAG_MAX_BLOCKS * TGV_DIAG_COUNT * sizeof(double);
+}
+
+int32_t tgv_init(const tgv_config* cfg, void* q, void* stream) {
+  int32_t s = check(cfg);
+  if (s != TGV_OK) return s;
+  if (!q) return TGV_ERR_ARG;
+  const Problem P = make_problem(*cfg);
+  TGV_CUDA_TRY(mode_launchers(find_mode(*cfg)).init(P, q, (cudaStream_t)stream));
+  return TGV_OK;
+}
+
+static int32_t launch_stage_common(const tgv_config* cfg, const StageArgs& S, bool rhs,
+                                   cudaStream_t st) {
+  const int m = find_mode(*cfg);
+  const ModeLaunchers& L = mode_launchers(m);
+  const int tile = pick_tile(*cfg);
+  const int dev = current_device();
+  if (dev < 0) return TGV_ERR_CUDA;
+  const int occ = stage_occ(dev, m, tile);
+  if (occ <= 0) return TGV_ERR_CUDA;
+  const int zc = pick_zchunk(*cfg, tile, occ, device_sms(dev));
+  StageArgs A = S;
+  A.zchunk = zc;
+  const Problem P = make_problem(*cfg);
+  cudaError_t e = rhs ? L.rhs[tile](P, A, zc, st) : L.stage[tile](P, A, zc, st);
+  return e == cudaSuccess ? TGV_OK : TGV_ERR_CUDA;
+}
+
+int32_t rhs_eval(const tgv_config* cfg, const void* q, void* r, void* stream) {
+  int32_t s = check(cfg);
+  if (s != TGV_OK) return s;
+  if (!q || !r || q == r) return TGV_ERR_ARG;
+  StageArgs S;
+  std::memset(&S, 0, sizeof(S));
+  S.q_in = q;
+  S.r_out = r;
+  return launch_stage_common(cfg, S, true, (cudaStream_t)stream);
+}
+
+int32_t rk_substep(const tgv_config* cfg, const void* q_in, void* q_out, void* qt, int32_t i,
+                   double dt, void* stream) {
+  int32_t s = check(cfg);
+  if (s != TGV_OK) return s;
+  if (!q_in || !q_out || !qt || q_in == q_out || i < 0 || i > 2 || !std::isfinite(dt))
+    return TGV_ERR_ARG;
+  StageArgs S;
+  std::memset(&S, 0, sizeof(S));
+  S.q_in = q_in;
+  S.q_out = q_out;
+  S.qt = qt;
+  S.a = RK_A[i];
+  S.b = RK_B[i];
+  S.dt = dt;
+  S.read_qt = (i != 0);
+  S.write_qt = 1;
+  return launch_stage_common(cfg, S, false, (cudaStream_t)stream);
+}
+
+int32_t diagnostics_reduce(const tgv_config* cfg, const void* q, double* out_dev, void* workspace,
+                           size_t ws_bytes, void* stream) {
+  int32_t s = check(cfg);
+  if (s != TGV_OK) return s;
+  if (!q || !out_dev) return TGV_ERR_ARG;
+  if (!workspace || ws_bytes < tgv_workspace_bytes(cfg)) return TGV_ERR_WORKSPACE;
+  const Problem P = make_problem(*cfg);
+  const long long n3 = (long long)cfg->n * cfg->n * cfg->n;
+  long long nb = (n3 + DIAG_THREADS - 1) / DIAG_THREADS;
+  if (nb > DIAG_MAX_BLOCKS) nb = DIAG_MAX_BLOCKS;
+  cudaStream_t st = (cudaStream_t)stream;
+  double* part = static_cast<double*>(workspace);
+  TGV_CUDA_TRY(mode_launchers(find_mode(*cfg)).diag_partial(P, q, part, (int)nb, st));
+  diag_final_kernel<<<1, 32 * TGV_DIAG_COUNT, 0, st>>>(P, part, (int)nb, out_dev);
+  TGV_CUDA_TRY(cudaGetLastError());
+  return TGV_OK;
+}
+
+int32_t rk_step(const tgv_config* cfg, void* q_a, void* q_b, void* qt, double dt, int32_t nsteps,
+                int32_t diag_every, double* diag_dev, void* workspace, size_t ws_bytes,
+                int32_t* parity_out, void* stream) {
+  int32_t s = check(cfg);
+  if (s != TGV_OK) return s;
+  if (!q_a || !q_b || !qt || q_a == q_b || nsteps < 0 || diag_every < 0 || !std::isfinite(dt) ||
+      !(dt > 0.0))
+    return TGV_ERR_ARG;
+  if (diag_every > 0) {
+    if (!diag_dev) return TGV_ERR_ARG;
+    if (!workspace || ws_bytes < tgv_workspace_bytes(cfg)) return TGV_ERR_WORKSPACE;
+  }
+  if (!(cfg->flags & TGV_FLAG_ALLOW_UNSTABLE_DT) && dt > tgv_dt_max(cfg)) return TGV_ERR_UNSTABLE_DT;
+  void* buf[2] = {q_a, q_b};
+  int cur = 0;
+  int rec = 0;
+  for (int32_t m = 0; m < nsteps; ++m) {
+    if (diag_every > 0 && m % diag_every == 0) {
+      s = diagnostics_reduce(cfg, buf[cur], diag_dev + (size_t)rec * TGV_DIAG_COUNT, workspace,
+                             ws_bytes, stream);
+      if (s != TGV_OK) return s;
+      ++rec;
+    }
+    for (int i = 0; i < 3; ++i) {
+      s = rk_substep(cfg, buf[cur], buf[cur ^ 1], qt, i, dt, stream);
+      if (s != TGV_OK) return s;
+      cur ^= 1;
+    }
+  }
+  if (diag_every > 0 && nsteps % diag_every == 0) {
+    s = diagnostics_reduce(cfg, buf[cur], diag_dev + (size_t)rec * TGV_DIAG_COUNT, workspace,
+                           ws_bytes, stream);
+    if (s != TGV_OK) return s;
+  }
+  if (parity_out) *parity_out = cur;
+  return TGV_OK;
+}
+
+static size_t up256(size_t b) { return (b + 255) & ~(size_t)255; }
+
+size_t tgv_run_host_workspace_bytes(const tgv_config* cfg, int32_t nsteps, int32_t diag_every) {
+  if (check(cfg) != TGV_OK || nsteps < 0 || diag_every < 0) return 0;
+  const size_t nrec = diag_every > 0 ? (size_t)(nsteps / diag_every + 1) : 0;
+  return 2 * up256(tgv_state_bytes(cfg)) + up256(tgv_qt_bytes(cfg)) +
+         up256(tgv_workspace_bytes(cfg)) + up256(nrec * TGV_DIAG_COUNT * sizeof(double));
+}
+
+int32_t tgv_run_host(const tgv_config* cfg, const void* q_host_in, void* q_host_out, double dt,
+                     int32_t nsteps, int32_t diag_every, double* diag_host, void* dev_workspace,
+                     size_t ws_bytes, void* stream) {
+  int32_t s = check(cfg);
+  if (s != TGV_OK) return s;
+  if (!q_host_in || !q_host_out || nsteps < 0 || diag_every < 0) return TGV_ERR_ARG;
+  if (!dev_workspace || ws_bytes < tgv_run_host_workspace_bytes(cfg, nsteps, diag_every))
+    return TGV_ERR_WORKSPACE;
+  const size_t qb = tgv_state_bytes(cfg), qtb = tgv_qt_bytes(cfg);
+  const size_t wsb = tgv_workspace_bytes(cfg);
+  char* w = static_cast<char*>(dev_workspace);
+  void* qa = w;
+  void* qbuf = w + up256(qb);
+  void* qt = w + 2 * up256(qb);
+  void* diag_ws = w + 2 * up256(qb) + up256(qtb);
+  double* diag_dev = reinterpret_cast<double*>(w + 2 * up256(qb) + up256(qtb) + up256(wsb));
+  const int nrec = diag_every > 0 ? nsteps / diag_every + 1 : 0;
+  cudaStream_t st = (cudaStream_t)stream;
+  TGV_CUDA_TRY(cudaMemcpyAsync(qa, q_host_in, qb, cudaMemcpyHostToDevice, st));
+  int32_t parity = 0;
+  s = rk_step(cfg, qa, qbuf, qt, dt, nsteps, diag_every, nrec > 0 ? diag_dev : nullptr, diag_ws,
+              wsb, &parity, stream);
+  if (s != TGV_OK) return s;
+  TGV_CUDA_TRY(cudaMemcpyAsync(q_host_out, parity ? qbuf : qa, qb, cudaMemcpyDeviceToHost, st));
+  if (nrec > 0 && diag_host)
+    TGV_CUDA_TRY(cudaMemcpyAsync(diag_host, diag_dev, (size_t)nrec * TGV_DIAG_COUNT * sizeof(double),
+                                 cudaMemcpyDeviceToHost, st));
+  TGV_CUDA_TRY(cudaStreamSynchronize(st));
+  return TGV_OK;
+}
+
+}  // extern "C"
+
+namespace tgv {
+__global__ void diag_final_kernel(const Problem P, const double* __restrict__ part, int nblocks,
+                                  double* __restrict__ out) {
+  // 32 lanes per diagnostic: each lane sums a fixed strided subset in order,
+  // then a fixed shuffle tree combines the lanes.
+  const int m = threadIdx.x / 32, lane = threadIdx.x % 32;
+  if (m >= TGV_DIAG_COUNT) return;
+  double v = 0.0;
+  const int src = (m == 3) ? 2 : m;  // eps^S = <omega.omega> / Re
+  for (int b = lane; b < nblocks; b += 32) v += part[b * TGV_DIAG_COUNT + src];
+  for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
+  if (lane == 0) {
+    const double n3 = (double)P.n * P.n * P.n;
+    if (m == 9) out[9] = v;
+    else if (m == 3) out[3] = v / n3 / P.re;
+    else out[m] = v / n3;
+  }
+}
+}  // namespace tgv

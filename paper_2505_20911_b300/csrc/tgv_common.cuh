@@ -1,0 +1,123 @@
+// tgv_common.cuh - shared device/host definitions of the TGV kernels.
+//
+// Number types: storage types (double, float, __nv_bfloat16, __half) convert
+// to and from the compute/accumulate types through the helpers below; all
+// arithmetic of a kernel runs in one compute type TC.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_fp16.h>
+#include <cuda_bf16.h>
+#include <stdint.h>
+
+#include "tgv.h"
+
+namespace tgv {
+
+// ---------------------------------------------------------------- conversions
+template <class T> struct Num;
+template <> struct Num<double> {
+  static __host__ __device__ __forceinline__ double to_f64(double v) { return v; }
+  static __host__ __device__ __forceinline__ double from_f64(double v) { return v; }
+};
+template <> struct Num<float> {
+  static __host__ __device__ __forceinline__ double to_f64(float v) { return (double)v; }
+  static __host__ __device__ __forceinline__ float from_f64(double v) { return (float)v; }
+};
+template <> struct Num<__half> {
+  static __device__ __forceinline__ double to_f64(__half v) { return (double)__half2float(v); }
+  static __device__ __forceinline__ __half from_f64(double v) { return __double2half(v); }
+};
+template <> struct Num<__nv_bfloat16> {
+  static __device__ __forceinline__ double to_f64(__nv_bfloat16 v) {
+    return (double)__bfloat162float(v);
+  }
+  static __device__ __forceinline__ __nv_bfloat16 from_f64(double v) {
+    return __double2bfloat16(v);
+  }
+};
+
+// cvt<To>(from): one rounding, from any supported type to any other.
+template <class To, class From> struct Cvt {
+  static __device__ __forceinline__ To go(From v) { return Num<To>::from_f64(Num<From>::to_f64(v)); }
+};
+template <class T> struct Cvt<T, T> {
+  static __device__ __forceinline__ T go(T v) { return v; }
+};
+template <> struct Cvt<float, __half> {
+  static __device__ __forceinline__ float go(__half v) { return __half2float(v); }
+};
+template <> struct Cvt<__half, float> {
+  static __device__ __forceinline__ __half go(float v) { return __float2half_rn(v); }
+};
+template <> struct Cvt<float, __nv_bfloat16> {
+  static __device__ __forceinline__ float go(__nv_bfloat16 v) { return __bfloat162float(v); }
+};
+template <> struct Cvt<__nv_bfloat16, float> {
+  static __device__ __forceinline__ __nv_bfloat16 go(float v) { return __float2bfloat16_rn(v); }
+};
+template <> struct Cvt<float, double> {
+  static __device__ __forceinline__ float go(double v) { return (float)v; }
+};
+template <> struct Cvt<double, float> {
+  static __device__ __forceinline__ double go(float v) { return (double)v; }
+};
+template <class To, class From>
+__device__ __forceinline__ To cvt(From v) { return Cvt<To, From>::go(v); }
+
+// Reciprocal in the compute type (IEEE-rounded division for float/double).
+__device__ __forceinline__ double recip(double v) { return 1.0 / v; }
+__device__ __forceinline__ float recip(float v) { return 1.0f / v; }
+__device__ __forceinline__ __half recip(__half v) { return hrcp(v); }
+
+template <class T> __device__ __forceinline__ bool finite_val(T v) {
+  double d = Num<T>::to_f64(v);
+  return isfinite(d);
+}
+
+// ------------------------------------------------------------ problem params
+// Per-problem constants, precomputed on the host in FP64.
+struct Problem {
+  int n;            // grid points per direction
+  int split;        // tgv_split
+  int encoding;     // tgv_encoding
+  double h;         // grid spacing L/N
+  double inv12h;    // 1/(12 h): first-derivative stencil scale
+  double inv12h2;   // 1/(12 h^2): second-derivative stencil scale
+  double gamma, gm1, gM2;  // gamma, gamma-1, gamma*M^2
+  double nu;        // mu/Re
+  double kappa;     // mu/((gamma-1) M^2 Pr Re)
+  double rho0, rhoE0;      // encoding offsets (0 for TGV_ENC_PLAIN)
+  double mach, re;
+};
+
+Problem make_problem(const tgv_config& c);
+
+// Storage-type tag -> C++ type.
+template <int D> struct DType;
+template <> struct DType<TGV_F64> { using T = double; };
+template <> struct DType<TGV_F32> { using T = float; };
+template <> struct DType<TGV_BF16> { using T = __nv_bfloat16; };
+template <> struct DType<TGV_F16> { using T = __half; };
+
+inline size_t dtype_size(int d) {
+  switch (d) {
+    case TGV_F64: return 8;
+    case TGV_F32: return 4;
+    case TGV_BF16: return 2;
+    case TGV_F16: return 2;
+  }
+  return 0;
+}
+
+// Williamson 2N coefficients (reading of Sec. 3.1, Eqs. 3-4).
+constexpr double RK_A[3] = {0.0, -5.0 / 9.0, -153.0 / 128.0};
+constexpr double RK_B[3] = {1.0 / 3.0, 15.0 / 16.0, 8.0 / 15.0};
+
+#define TGV_CUDA_TRY(expr)                                    \
+  do {                                                        \
+    cudaError_t e__ = (expr);                                 \
+    if (e__ != cudaSuccess) { return TGV_ERR_CUDA; }          \
+  } while (0)
+
+}  // namespace tgv
