@@ -1,0 +1,423 @@
+"""Benchmark of the TGV hot path on B300: grid-point-steps/s per precision mode.
+
+Workload (default): the 256^3 Taylor-Green precision sweep - periodic
+[0, 2pi]^3, M = 0.1, Re = 1600, Pr = 0.71, gamma = 1.4, 4th-order central
+differences with the Blaisdell split, low-storage RK3, dt = 0.00125 (the
+stable step at 256^3), kinetic energy and enstrophy reduced in FP64 every 10
+steps.  One bench step = one RK3 time step (three fused stage launches) plus
+its share of the diagnostics.  The headline `value` is the half-single mode
+(FP16 storage, FP32 compute, offset encoding); every other mode of the sweep
+is timed in the same run and reported under "modes" next to FP64.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+Under torchrun (N > 1) every rank advances its own replica (weak scaling, no
+collective on the data path); value = all ranks' point-steps / max time.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "TGV grid-point-steps/s per precision mode vs FP64 on same B300; % of HBM peak"
+UNIT = "grid-point-steps/s"
+N_DEFAULT = 256
+DT_DEFAULT = 0.00125
+DIAG_EVERY = 10
+HEADLINE = "fp16_fp32"
+SWEEP = ("fp64", "spdp", "fp32s_fp64c", "fp32", "bf16_fp32", "fp16_fp32", "fp16", "hpsp")
+OFFSET_MODES = ("bf16_fp32", "fp16_fp32", "fp16")
+STAGE_SRC = os.path.join(ROOT, "paper_2505_20911_b300", "csrc", "tgv_stage.cuh")
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--n", type=int, default=N_DEFAULT)
+    ap.add_argument("--no-sweep", action="store_true", help="headline mode only")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-baseline leg")
+    ap.add_argument("--profile-case", default=None, metavar="MODE",
+                    help="run 2 warm-up RK3 steps and 1 more step of MODE at --n, then exit "
+                         "(the small case an ncu capture of the stage kernel uses)")
+    return ap.parse_args()
+
+
+def profile_case(args):
+    """Launches: 1 init, 6 warm-up stage launches, then 3 stage launches."""
+    import torch
+    import paper_2505_20911_b300 as tgv
+    cfg = mode_config(tgv, args.n, args.profile_case)
+    qa = tgv.empty_state(cfg)
+    qb = torch.empty_like(qa)
+    qt = tgv.empty_qt(cfg)
+    tgv.tgv_init(cfg, qa)
+    dt = DT_DEFAULT * 256.0 / args.n
+    tgv.rk_step(cfg, qa, qb, qt, dt, 2)
+    tgv.rk_step(cfg, qa, qb, qt, dt, 1)
+    torch.cuda.synchronize()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+# --------------------------------------------------------------------- clocks
+class ClockSampler:
+    """nvidia-smi samples (SM clock, throttle reasons) during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self._t = threading.Thread(target=self._read, daemon=True)
+            self._t.start()
+        except OSError:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, smax, reasons = [], [], set()
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---------------------------------------------------------------- our GPU arm
+def alg_bytes_per_point_step(cfg, torch):
+    s = torch.tensor([], dtype=cfg.q_dtype).element_size()
+    st = torch.tensor([], dtype=cfg.qt_dtype).element_size()
+    # per step: Q read+written by all 3 stages (30 s), Qt written by stages 1-2
+    # and read by stages 2-3 (20 st)
+    return 30 * s + 20 * st
+
+
+def mode_config(tgv, n, mode):
+    return tgv.Config(n=n, mode=mode, encoding="offset" if mode in OFFSET_MODES else "plain")
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            return json.load(fh), "measured"
+    except OSError:
+        return {"hbm_gbs": 6400.0, "bf16_tflops": 1800.0}, "fallback"
+
+
+def profile_traffic(mode, n):
+    """dram read+write bytes per stage launch from the committed ncu summary,
+    if the stage kernel source is unchanged since the capture; else None."""
+    path = os.path.join(ROOT, "profiles", f"stage_kernel_{mode}_{n}.md")
+    try:
+        text = open(path).read()
+    except OSError:
+        return None
+    sha = hashlib.sha256(open(STAGE_SRC, "rb").read()).hexdigest()[:16]
+    vals = {}
+    for line in text.splitlines():
+        if ":" in line and line.strip().startswith("- "):
+            k, v = line.strip()[2:].split(":", 1)
+            vals[k.strip()] = v.strip().strip("`")
+    if vals.get("stage_source_sha256_16") != sha:
+        return None
+    try:
+        return float(vals["traffic_bytes_per_launch"])
+    except (KeyError, ValueError):
+        return None
+
+
+def run_ours(args, rank, world, local):
+    import torch
+    import paper_2505_20911_b300 as tgv
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    def max_over_ranks(v):
+        if dist is None:
+            return v
+        t = torch.tensor([v], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    n, dt, K, W = args.n, DT_DEFAULT * (256.0 / args.n), args.steps, max(args.warmup, 3)
+    stream = torch.cuda.current_stream()
+
+    def setup(mode):
+        cfg = mode_config(tgv, n, mode)
+        qa = tgv.empty_state(cfg, dev)
+        qb = torch.empty_like(qa)
+        qt = tgv.empty_qt(cfg, dev)
+        ws = tgv.empty_workspace(cfg, dev)
+        tgv.tgv_init(cfg, qa)
+        return cfg, qa, qb, qt, ws
+
+    def timed_steps(cfg, qa, qb, qt, ws, steps, diag_every):
+        nrec = steps // diag_every + 1 if diag_every else 0
+        diag = torch.empty(max(nrec, 1), tgv.TGV_DIAG_COUNT, dtype=torch.float64, device=dev)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        barrier()
+        e0.record(stream)
+        par = tgv.rk_step(cfg, qa, qb, qt, dt, steps, diag_every, diag if nrec else None, ws,
+                          stream)
+        e1.record(stream)
+        barrier()
+        return e0.elapsed_time(e1), par, diag, nrec
+
+    # ---- headline mode: warm-up, then the timed region with clock sampling
+    cfg, qa, qb, qt, ws = setup(HEADLINE)
+    tgv.rk_step(cfg, qa, qb, qt, dt, W, DIAG_EVERY, torch.empty(W // DIAG_EVERY + 1,
+                tgv.TGV_DIAG_COUNT, dtype=torch.float64, device=dev), ws, stream)
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        ms, par, diag, nrec = timed_steps(cfg, qa, qb, qt, ws, K, DIAG_EVERY)
+    ms = max_over_ranks(ms)
+    ms_step = ms / K
+    value = world * n ** 3 * K / (ms * 1e-3)
+    diag_last = diag[nrec - 1].cpu().tolist()
+    launches = 3 * K + 2 * nrec
+
+    # ---- roofline of the dominant kernel (the fused stage), on the same stream
+    reps = max(10, min(K, 60))
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    bufs = [qa, qb]
+    cur = 0
+    barrier()
+    e0.record(stream)
+    for r in range(reps):
+        for i in range(3):
+            tgv.rk_substep(cfg, bufs[cur], bufs[cur ^ 1], qt, i, dt, stream)
+            cur ^= 1
+    e1.record(stream)
+    barrier()
+    stage_ms = e0.elapsed_time(e1) / (3 * reps)
+    bpp = alg_bytes_per_point_step(cfg, torch)
+    alg_bytes_launch = bpp / 3.0 * n ** 3
+    peaks, peak_kind = measured_peaks()
+    achieved = alg_bytes_launch / (stage_ms * 1e-3) / 1e9
+    roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peaks["hbm_gbs"],
+                "unit": "GB/s", "frac": round(achieved / peaks["hbm_gbs"], 4),
+                "traffic": profile_traffic(HEADLINE, n), "peak_kind": f"{peak_kind} hbm_gbs",
+                "kernel": "stage_kernel (fused RHS + RK stage)", "stage_ms": round(stage_ms, 4),
+                "alg_bytes_per_launch": alg_bytes_launch}
+    del qa, qb, qt
+    torch.cuda.empty_cache()
+
+    # ---- e2e: the public host-buffer call (H2D of Q, 10 steps, D2H of Q + diagnostics)
+    e2e = None
+    try:
+        cfg = mode_config(tgv, n, HEADLINE)
+        qh_in = torch.empty((5, n, n, n), dtype=cfg.q_dtype).pin_memory()
+        qdev = tgv.empty_state(cfg, dev)
+        tgv.tgv_init(cfg, qdev)
+        qh_in.copy_(qdev)
+        del qdev
+        qh_out = torch.empty_like(qh_in).pin_memory()
+        calls, steps_per_call = 4, DIAG_EVERY
+        nrec = steps_per_call // DIAG_EVERY + 1
+        dh = torch.empty(nrec * tgv.TGV_DIAG_COUNT, dtype=torch.float64).pin_memory()
+        wsb = tgv.tgv_run_host_workspace_bytes(cfg, steps_per_call, DIAG_EVERY)
+        dws = torch.empty(wsb, dtype=torch.uint8, device=dev)
+        tgv.tgv_run_host(cfg, qh_in, qh_out, dt, steps_per_call, DIAG_EVERY, dh, dws, stream)
+        barrier()
+        t0 = time.perf_counter()
+        for _ in range(calls):
+            tgv.tgv_run_host(cfg, qh_in, qh_out, dt, steps_per_call, DIAG_EVERY, dh, dws, stream)
+        barrier()
+        el = max_over_ranks(time.perf_counter() - t0)
+        qbytes = tgv.tgv_state_bytes(cfg)
+        e2e = {"value": world * n ** 3 * steps_per_call * calls / el, "unit": UNIT,
+               "h2d_bytes_per_step": qbytes / steps_per_call,
+               "d2h_bytes_per_step": (qbytes + dh.numel() * 8) / steps_per_call,
+               "call": f"tgv_run_host: H2D of Q, {steps_per_call} RK3 steps with FP64 "
+                       f"diagnostics, D2H of Q and diagnostics, from pinned host memory"}
+        del dws
+        torch.cuda.empty_cache()
+    except Exception as exc:  # report, do not hide
+        e2e = {"value": None, "unit": UNIT, "error": repr(exc)}
+
+    # ---- the rest of the precision sweep, each next to FP64
+    modes = {}
+    if not args.no_sweep:
+        for mode in SWEEP:
+            c, a, b, t, w = setup(mode)
+            steps = 4 if c.compute_dtype == torch.float64 and mode != "spdp" else 20
+            tgv.rk_step(c, a, b, t, dt, 2, 0, None, None, stream)
+            m_ms, _, _, _ = timed_steps(c, a, b, t, w, steps, DIAG_EVERY if steps >= 10 else 0)
+            m_ms = max_over_ranks(m_ms)
+            v = world * n ** 3 * steps / (m_ms * 1e-3)
+            bpp_m = alg_bytes_per_point_step(c, torch)
+            modes[mode] = {"value": v, "ms_per_step": m_ms / steps, "steps": steps,
+                           "alg_GBs": bpp_m * v / world / 1e9,
+                           "hbm_frac": bpp_m * v / world / 1e9 / peaks["hbm_gbs"],
+                           "bytes_per_point_step": bpp_m}
+            del a, b, t, w
+            torch.cuda.empty_cache()
+        for mode in modes:
+            modes[mode]["vs_fp64"] = modes[mode]["value"] / modes["fp64"]["value"]
+
+    if dist is not None:
+        dist.destroy_process_group()
+    return {
+        "value": value, "ms_per_step": ms_step, "roofline": roofline, "e2e": e2e,
+        "gpu_launches": launches, "clocks": clk.summary(), "modes": modes,
+        "diag_last": dict(zip(tgv.DIAG_NAMES, diag_last)), "dt": dt,
+    }
+
+
+# ------------------------------------------------------------ CPU oracle legs
+def oracle_sample(n_sample, steps=1):
+    """Time `steps` RK3 steps of the FP64 oracle on an n_sample^3 TGV."""
+    import torch
+    import oracle
+    flow = oracle.Flow(n=n_sample)
+    q = oracle.initial_condition(flow)
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        q = oracle.rk3_step(flow, q, DT_DEFAULT * 256.0 / n_sample)
+    el = time.perf_counter() - t0
+    return n_sample ** 3 * steps / el, el
+
+
+def cpu_baseline(n):
+    import torch
+    v, el = oracle_sample(n, 1)
+    return {"value": v, "unit": UNIT, "cores": torch.get_num_threads(), "kind": "oracle",
+            "sample": f"1 RK3 step of the FP64 oracle on the full {n}^3 TGV grid "
+                      f"({el:.1f} s on the host cores)"}
+
+
+def run_reference(args, rank, world):
+    """The oracle (plain FP64 PyTorch CPU code) on the same metric and config;
+    each step is one RK3 step on an n_s^3 TGV sized so K+W steps fit ~150 s."""
+    import torch
+    if rank != 0:
+        return None
+    K, W = args.steps, max(args.warmup, 3)
+    # calibrate the per-point cost on a small grid, then size the sample
+    rate, _ = oracle_sample(24, 1)
+    budget = 150.0 / (K + W)
+    n_s = 16
+    for cand in (16, 24, 32, 48, 64, 96, 128, 192, 256):
+        if cand ** 3 / rate <= budget:
+            n_s = cand
+    import oracle
+    flow = oracle.Flow(n=n_s)
+    q = oracle.initial_condition(flow)
+    dt = DT_DEFAULT * 256.0 / n_s
+    for _ in range(W):
+        q = oracle.rk3_step(flow, q, dt)
+    t0 = time.perf_counter()
+    for _ in range(K):
+        q = oracle.rk3_step(flow, q, dt)
+    el = time.perf_counter() - t0
+    value = n_s ** 3 * K / el
+    cores = torch.get_num_threads()
+    sample = f"{K} RK3 steps of the FP64 oracle on a {n_s}^3 TGV (same physics), {cores} threads"
+    return {"value": value, "ms_per_step": el * 1e3 / K, "sample": sample, "cores": cores}
+
+
+def main():
+    args = parse()
+    if args.profile_case:
+        profile_case(args)
+        return
+    rank, world, local = dist_env()
+    base = {"metric": METRIC, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": max(args.warmup, 3), "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "data": "synthetic (analytic Taylor-Green initial field)"}
+    config = {"workload": f"TGV {args.n}^3 precision sweep (headline: half-single, FP16 "
+                          f"storage / FP32 compute, offset encoding)",
+              "n": args.n, "M": 0.1, "Re": 1600.0, "Pr": 0.71, "gamma": 1.4,
+              "dt": DT_DEFAULT * 256.0 / args.n, "diag_every": DIAG_EVERY,
+              "split": "blaisdell", "l2": "inputs larger than L2: Q in, Q out and Qt of the "
+                                          "headline mode are each above 126 MB at 256^3",
+              "parallelism": f"replicas x{world}"}
+    if args.impl == "reference":
+        ref = run_reference(args, rank, world)
+        if rank == 0:
+            line = dict(base, impl="reference", value=ref["value"],
+                        ms_per_step=ref["ms_per_step"], dtype="f64", config=config,
+                        cpu_baseline={"value": ref["value"], "unit": UNIT, "cores": ref["cores"],
+                                      "kind": "oracle", "sample": ref["sample"]},
+                        e2e={"value": ref["value"], "unit": UNIT, "h2d_bytes_per_step": 0,
+                             "d2h_bytes_per_step": 0})
+            print(json.dumps(line), flush=True)
+        return
+    res = run_ours(args, rank, world, local)
+    if rank != 0:
+        return
+    line = dict(base, value=res["value"], ms_per_step=res["ms_per_step"], dtype="f32",
+                config=config, roofline=res["roofline"], e2e=res["e2e"],
+                gpu_launches=res["gpu_launches"], clocks=res["clocks"], modes=res["modes"],
+                diag_last=res["diag_last"])
+    if world == 1 and not args.no_cpu:
+        line["cpu_baseline"] = cpu_baseline(args.n)
+    print(json.dumps(line), flush=True)
+
+
+if __name__ == "__main__":
+    main()
