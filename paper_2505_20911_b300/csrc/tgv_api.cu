@@ -70,7 +70,7 @@ static bool valid_dtype(int d) { return d >= TGV_F64 && d <= TGV_F16; }
 
 static int32_t check(const tgv_config* c) {
   if (!c) return TGV_ERR_ARG;
-  if (c->n < 8 || c->n > 1024) return TGV_ERR_ARG;
+  if (c->n < 8 || c->n > 1024 || (c->n & 1)) return TGV_ERR_ARG;
   if (c->split_form != TGV_SPLIT_BLAISDELL && c->split_form != TGV_SPLIT_DIVERGENCE) return TGV_ERR_ARG;
   if (!valid_dtype(c->q_storage) || !valid_dtype(c->qt_storage) || !valid_dtype(c->compute) ||
       !valid_dtype(c->accumulate))
@@ -86,11 +86,29 @@ static int32_t check(const tgv_config* c) {
   return TGV_OK;
 }
 
-// Default tile per mode: 32x8 when N fills it, else 16x8.
+// Default tile: among the tiles whose shared memory fits, the one that pads
+// N x N least (ties go to the larger tile).  -1 if none fits.
 static int pick_tile(const tgv_config& c) {
-  if (c.tile > 0) return c.tile - 1;
-  if (c.n % 32 == 0) return 0;
-  return 2;
+  const ModeLaunchers& L = mode_launchers(find_mode(c));
+  if (c.tile > 0) return L.smem[c.tile - 1] <= STAGE_SMEM_LIMIT ? c.tile - 1 : -1;
+  int best = -1;
+  long long best_area = -1;
+  for (int t = 0; t < NUM_TILES; ++t) {
+    if (L.smem[t] > STAGE_SMEM_LIMIT) continue;
+    const int tx = tile_tx(c.compute, t), ty = tile_ty(c.compute, t);
+    const long long area = (long long)((c.n + tx - 1) / tx) * tx * ((c.n + ty - 1) / ty) * ty;
+    if (best_area < 0 || area < best_area) { best_area = area; best = t; }
+  }
+  return best;
+}
+
+// Upper bound on the z chunks of one stage launch (bounds the CTA count, and
+// with it the diagnostics partials of a fused launch).
+constexpr int MAX_ZCHUNKS = 16;
+
+static long long stage_ctas(const tgv_config& c, int tile, int zc) {
+  const int tx = tile_tx(c.compute, tile), ty = tile_ty(c.compute, tile);
+  return (long long)((c.n + tx - 1) / tx) * ((c.n + ty - 1) / ty) * ((c.n + zc - 1) / zc);
 }
 
 // Per-device caches (SM count; resident CTAs per SM of each stage kernel).
@@ -125,12 +143,12 @@ static int stage_occ(int dev, int mode, int tile) {
 static int pick_zchunk(const tgv_config& c, int tile, int occupancy, int sms) {
   if (c.zchunk > 0) return c.zchunk;
   const int n = c.n;
-  const int tx = TILE_TX[tile], ty = TILE_TY[tile];
+  const int tx = tile_tx(c.compute, tile), ty = tile_ty(c.compute, tile);
   const long long tiles = (long long)((n + tx - 1) / tx) * ((n + ty - 1) / ty);
   const long long conc = (long long)(occupancy > 0 ? occupancy : 1) * (sms > 0 ? sms : 148);
   double best = -1.0;
   int best_zc = n;
-  for (int chunks = 1; chunks <= n / 8; ++chunks) {
+  for (int chunks = 1; chunks <= n / 8 && chunks <= MAX_ZCHUNKS; ++chunks) {
     const int zc = (n + chunks - 1) / chunks;
     const long long ctas = tiles * ((n + zc - 1) / zc);
     const long long waves = (ctas + conc - 1) / conc;
@@ -181,7 +199,7 @@ int32_t tgv_tile_count(void) { return NUM_TILES; }
 
 int32_t tgv_tile_shape(int32_t t, int32_t* tx, int32_t* ty) {
   if (t < 1 || t > NUM_TILES || !tx || !ty) return TGV_ERR_ARG;
-  *tx = TILE_TX[t - 1];
+  *tx = TILE_TX[t - 1];  // FP32/FP16 compute; FP64 compute uses TILE_TX_F64
   *ty = TILE_TY[t - 1];
   return TGV_OK;
 }
@@ -196,7 +214,13 @@ double tgv_dt_max(const tgv_config* cfg) {
 
 size_t tgv_workspace_bytes(const tgv_config* cfg) {
   if (check(cfg) != TGV_OK) return 0;
-  return (size_t)DIAG_MAX_BLOCKS * TGV_DIAG_COUNT * sizeof(double);
+  long long blocks = DIAG_MAX_BLOCKS;
+  for (int t = 0; t < NUM_TILES; ++t) {
+    const int zc = cfg->zchunk > 0 ? cfg->zchunk : (cfg->n + MAX_ZCHUNKS - 1) / MAX_ZCHUNKS;
+    const long long b = stage_ctas(*cfg, t, zc);
+    if (b > blocks) blocks = b;
+  }
+  return (size_t)blocks * TGV_DIAG_COUNT * sizeof(double);
 }
 
 int32_t tgv_init(const tgv_config* cfg, void* q, void* stream) {
@@ -208,11 +232,14 @@ int32_t tgv_init(const tgv_config* cfg, void* q, void* stream) {
   return TGV_OK;
 }
 
+// Launch one stage kernel (rhs: residual epilogue; S.diag_part != nullptr:
+// the fused-diagnostics variant, whose CTA count is returned in *ctas).
 static int32_t launch_stage_common(const tgv_config* cfg, const StageArgs& S, bool rhs,
-                                   cudaStream_t st) {
+                                   cudaStream_t st, long long* ctas = nullptr) {
   const int m = find_mode(*cfg);
   const ModeLaunchers& L = mode_launchers(m);
   const int tile = pick_tile(*cfg);
+  if (tile < 0) return TGV_ERR_UNSUPPORTED;
   const int dev = current_device();
   if (dev < 0) return TGV_ERR_CUDA;
   const int occ = stage_occ(dev, m, tile);
@@ -221,7 +248,9 @@ static int32_t launch_stage_common(const tgv_config* cfg, const StageArgs& S, bo
   StageArgs A = S;
   A.zchunk = zc;
   const Problem P = make_problem(*cfg);
-  cudaError_t e = rhs ? L.rhs[tile](P, A, zc, st) : L.stage[tile](P, A, zc, st);
+  if (ctas) *ctas = stage_ctas(*cfg, tile, zc);
+  cudaError_t e = rhs ? L.rhs[tile](P, A, zc, st)
+                      : (S.diag_part ? L.stage_diag[tile](P, A, zc, st) : L.stage[tile](P, A, zc, st));
   return e == cudaSuccess ? TGV_OK : TGV_ERR_CUDA;
 }
 
@@ -236,23 +265,30 @@ int32_t rhs_eval(const tgv_config* cfg, const void* q, void* r, void* stream) {
   return launch_stage_common(cfg, S, true, (cudaStream_t)stream);
 }
 
+static int32_t substep_impl(const tgv_config* cfg, const void* q_in, void* q_out, void* qt,
+                            int32_t i, double dt, double* diag_part, long long* ctas,
+                            void* stream) {
+  StageArgs S;
+  std::memset(&S, 0, sizeof(S));
+  S.q_in = q_in;
+  S.q_out = q_out;
+  S.qt = qt;
+  S.diag_part = diag_part;
+  S.a = RK_A[i];
+  S.b = RK_B[i];
+  S.dt = dt;
+  S.read_qt = (i != 0);
+  S.write_qt = 1;
+  return launch_stage_common(cfg, S, false, (cudaStream_t)stream, ctas);
+}
+
 int32_t rk_substep(const tgv_config* cfg, const void* q_in, void* q_out, void* qt, int32_t i,
                    double dt, void* stream) {
   int32_t s = check(cfg);
   if (s != TGV_OK) return s;
   if (!q_in || !q_out || !qt || q_in == q_out || i < 0 || i > 2 || !std::isfinite(dt))
     return TGV_ERR_ARG;
-  StageArgs S;
-  std::memset(&S, 0, sizeof(S));
-  S.q_in = q_in;
-  S.q_out = q_out;
-  S.qt = qt;
-  S.a = RK_A[i];
-  S.b = RK_B[i];
-  S.dt = dt;
-  S.read_qt = (i != 0);
-  S.write_qt = 1;
-  return launch_stage_common(cfg, S, false, (cudaStream_t)stream);
+  return substep_impl(cfg, q_in, q_out, qt, i, dt, nullptr, nullptr, stream);
 }
 
 int32_t diagnostics_reduce(const tgv_config* cfg, const void* q, double* out_dev, void* workspace,
@@ -262,9 +298,9 @@ int32_t diagnostics_reduce(const tgv_config* cfg, const void* q, double* out_dev
   if (!q || !out_dev) return TGV_ERR_ARG;
   if (!workspace || ws_bytes < tgv_workspace_bytes(cfg)) return TGV_ERR_WORKSPACE;
   const Problem P = make_problem(*cfg);
-  const long long n3 = (long long)cfg->n * cfg->n * cfg->n;
-  long long nb = (n3 + DIAG_THREADS - 1) / DIAG_THREADS;
-  if (nb > DIAG_MAX_BLOCKS) nb = DIAG_MAX_BLOCKS;
+  const long long items = (long long)((cfg->n + DIAG_TX - 1) / DIAG_TX) *
+                          ((cfg->n + DIAG_TY - 1) / DIAG_TY) * cfg->n;
+  const long long nb = items < DIAG_MAX_BLOCKS ? items : DIAG_MAX_BLOCKS;
   cudaStream_t st = (cudaStream_t)stream;
   double* part = static_cast<double*>(workspace);
   TGV_CUDA_TRY(mode_launchers(find_mode(*cfg)).diag_partial(P, q, part, (int)nb, st));
@@ -289,16 +325,21 @@ int32_t rk_step(const tgv_config* cfg, void* q_a, void* q_b, void* qt, double dt
   void* buf[2] = {q_a, q_b};
   int cur = 0;
   int rec = 0;
+  const Problem P = make_problem(*cfg);
   for (int32_t m = 0; m < nsteps; ++m) {
-    if (diag_every > 0 && m % diag_every == 0) {
-      s = diagnostics_reduce(cfg, buf[cur], diag_dev + (size_t)rec * TGV_DIAG_COUNT, workspace,
-                             ws_bytes, stream);
-      if (s != TGV_OK) return s;
-      ++rec;
-    }
+    const bool log = diag_every > 0 && m % diag_every == 0;
     for (int i = 0; i < 3; ++i) {
-      s = rk_substep(cfg, buf[cur], buf[cur ^ 1], qt, i, dt, stream);
+      // the first substep of a logged step also reduces the diagnostics of Q^m
+      long long ctas = 0;
+      double* part = (log && i == 0) ? static_cast<double*>(workspace) : nullptr;
+      s = substep_impl(cfg, buf[cur], buf[cur ^ 1], qt, i, dt, part, &ctas, stream);
       if (s != TGV_OK) return s;
+      if (part) {
+        diag_final_kernel<<<1, 32 * TGV_DIAG_COUNT, 0, (cudaStream_t)stream>>>(
+            P, part, (int)ctas, diag_dev + (size_t)rec * TGV_DIAG_COUNT);
+        TGV_CUDA_TRY(cudaGetLastError());
+        ++rec;
+      }
       cur ^= 1;
     }
   }

@@ -31,88 +31,102 @@ __global__ void init_kernel(const Problem P, TS* __restrict__ q) {
   }
 }
 
-constexpr int DIAG_THREADS = 256;
+constexpr int DIAG_TX = 32, DIAG_TY = 8, DIAG_THREADS = DIAG_TX * DIAG_TY;
 constexpr int DIAG_MAX_BLOCKS = 148 * 8;
 
-template <class TS>
+// Per-point arithmetic type of the standalone diagnostics: FP64 for FP64
+// compute, FP32 otherwise (the sums are FP64 in every mode).
+template <class TC> struct DiagT { using T = float; };
+template <> struct DiagT<double> { using T = double; };
+
+template <class TS, class DT>
 __device__ __forceinline__ void load_vel(const TS* __restrict__ q, long long o, long long n3,
-                                         double rho0, double* u) {
-  const double rho = Num<TS>::to_f64(q[o]) + rho0;
-  u[0] = Num<TS>::to_f64(q[o + n3]) / rho;
-  u[1] = Num<TS>::to_f64(q[o + 2 * n3]) / rho;
-  u[2] = Num<TS>::to_f64(q[o + 3 * n3]) / rho;
+                                         DT rho0, DT* u) {
+  const DT rho = (DT)Num<TS>::to_f64(q[o]) + rho0;
+  const DT ri = DT(1) / rho;
+  u[0] = (DT)Num<TS>::to_f64(q[o + n3]) * ri;
+  u[1] = (DT)Num<TS>::to_f64(q[o + 2 * n3]) * ri;
+  u[2] = (DT)Num<TS>::to_f64(q[o + 3 * n3]) * ri;
 }
 
 // Per-block FP64 partial sums of the TGV_DIAG_COUNT diagnostics (sums, not
-// means); a fixed grid-stride assignment keeps the result deterministic.
-template <class TS>
+// means).  Work items are (32 x 8 tile, z plane) pairs, assigned to blocks in
+// a fixed grid-stride order, so the result is deterministic.
+template <class TS, class TC>
 __global__ void __launch_bounds__(DIAG_THREADS)
 diag_partial_kernel(const Problem P, const TS* __restrict__ q, double* __restrict__ part) {
+  using DT = typename DiagT<TC>::T;
   const int n = P.n;
   const long long nn = (long long)n * n, n3 = nn * n;
+  const int tilesx = (n + DIAG_TX - 1) / DIAG_TX, tilesy = (n + DIAG_TY - 1) / DIAG_TY;
+  const long long items = (long long)tilesx * tilesy * n;
+  const DT s = (DT)P.inv12h, rho0 = (DT)P.rho0, rhoE0 = (DT)P.rhoE0;
   double acc[TGV_DIAG_COUNT];
 #pragma unroll
   for (int m = 0; m < TGV_DIAG_COUNT; ++m) acc[m] = 0.0;
-  const double s = P.inv12h;
-  for (long long o = blockIdx.x * (long long)blockDim.x + threadIdx.x; o < n3;
-       o += (long long)gridDim.x * blockDim.x) {
-    const int i = (int)(o % n), j = (int)((o / n) % n), k = (int)(o / nn);
-    double qc[5];
+  for (long long item = blockIdx.x; item < items; item += gridDim.x) {
+    const int k = (int)(item / (tilesx * tilesy));
+    const int t = (int)(item - (long long)k * tilesx * tilesy);
+    const int i = (t % tilesx) * DIAG_TX + threadIdx.x;
+    const int j = (t / tilesx) * DIAG_TY + threadIdx.y;
+    if (i >= n || j >= n) continue;
+    const long long o = (long long)k * nn + (long long)j * n + i;
+    DT qc[5];
 #pragma unroll
-    for (int c = 0; c < 5; ++c) qc[c] = Num<TS>::to_f64(q[o + c * n3]);
-    qc[0] += P.rho0;
-    qc[4] += P.rhoE0;
+    for (int c = 0; c < 5; ++c) qc[c] = (DT)Num<TS>::to_f64(q[o + c * n3]);
+    qc[0] += rho0;
+    qc[4] += rhoE0;
     bool bad = false;
 #pragma unroll
-    for (int c = 0; c < 5; ++c) bad |= !isfinite(qc[c]);
-    const double u = qc[1] / qc[0], v = qc[2] / qc[0], w = qc[3] / qc[0];
-    const double u2 = u * u + v * v + w * w;
-    // velocity derivatives du_a/dx_b (4th-order central, periodic)
-    double g[3][3];  // g[a][b] = D_b u_a
+    for (int c = 0; c < 5; ++c) bad |= !isfinite((double)qc[c]);
+    const DT ri = DT(1) / qc[0];
+    const DT u = qc[1] * ri, v = qc[2] * ri, w = qc[3] * ri;
+    const DT u2 = u * u + v * v + w * w;
+    DT g[3][3];  // g[a][b] = D_b u_a
 #pragma unroll
     for (int b = 0; b < 3; ++b) {
-      double um2[3], um1[3], up1[3], up2[3];
-      const int ii[4] = {-2, -1, 1, 2};
-      double* dst[4] = {um2, um1, up1, up2};
+      DT um2[3], um1[3], up1[3], up2[3];
+      DT* dst[4] = {um2, um1, up1, up2};
+      const int off[4] = {-2, -1, 1, 2};
 #pragma unroll
-      for (int t = 0; t < 4; ++t) {
+      for (int tt = 0; tt < 4; ++tt) {
         int xi = i, yj = j, zk = k;
-        if (b == 0) xi = (i + ii[t] + n) % n;
-        if (b == 1) yj = (j + ii[t] + n) % n;
-        if (b == 2) zk = (k + ii[t] + n) % n;
-        load_vel(q, (long long)zk * nn + (long long)yj * n + xi, n3, P.rho0, dst[t]);
+        int* c = (b == 0) ? &xi : (b == 1) ? &yj : &zk;
+        *c += off[tt];
+        if (*c < 0) *c += n;
+        if (*c >= n) *c -= n;
+        load_vel<TS, DT>(q, (long long)zk * nn + (long long)yj * n + xi, n3, rho0, dst[tt]);
       }
 #pragma unroll
-      for (int a = 0; a < 3; ++a)
-        g[a][b] = s * (8.0 * (up1[a] - um1[a]) - (up2[a] - um2[a]));
+      for (int a = 0; a < 3; ++a) g[a][b] = s * (DT(8) * (up1[a] - um1[a]) - (up2[a] - um2[a]));
     }
-    const double wx = g[2][1] - g[1][2], wy = g[0][2] - g[2][0], wz = g[1][0] - g[0][1];
-    const double ens = wx * wx + wy * wy + wz * wz;
-    acc[0] += 0.5 * u2;
-    acc[1] += 0.5 * qc[0] * u2;
-    acc[2] += ens;
-    acc[4] += qc[0];
-    acc[5] += qc[1];
-    acc[6] += qc[2];
-    acc[7] += qc[3];
-    acc[8] += qc[4];
+    const DT wx = g[2][1] - g[1][2], wy = g[0][2] - g[2][0], wz = g[1][0] - g[0][1];
+    acc[0] += (double)(DT(0.5) * u2);
+    acc[1] += (double)(DT(0.5) * qc[0] * u2);
+    acc[2] += (double)(wx * wx + wy * wy + wz * wz);
+    acc[4] += (double)qc[0];
+    acc[5] += (double)qc[1];
+    acc[6] += (double)qc[2];
+    acc[7] += (double)qc[3];
+    acc[8] += (double)qc[4];
     acc[9] += bad ? 1.0 : 0.0;
   }
   // block reduction: warp shuffles, then a fixed-order pass over warps
   __shared__ double red[DIAG_THREADS / 32][TGV_DIAG_COUNT];
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int tid = threadIdx.y * DIAG_TX + threadIdx.x;
+  const int lane = tid & 31, warp = tid >> 5;
 #pragma unroll
   for (int m = 0; m < TGV_DIAG_COUNT; ++m) {
     double v = acc[m];
 #pragma unroll
-    for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
+    for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
     if (lane == 0) red[warp][m] = v;
   }
   __syncthreads();
-  if (threadIdx.x < TGV_DIAG_COUNT) {
+  if (tid < TGV_DIAG_COUNT) {
     double v = 0.0;
-    for (int w = 0; w < DIAG_THREADS / 32; ++w) v += red[w][threadIdx.x];
-    part[blockIdx.x * TGV_DIAG_COUNT + threadIdx.x] = v;
+    for (int w = 0; w < DIAG_THREADS / 32; ++w) v += red[w][tid];
+    part[blockIdx.x * TGV_DIAG_COUNT + tid] = v;
   }
 }
 

@@ -3,7 +3,7 @@
 // Each built (q_storage, qt_storage, compute, accumulate) combination is one
 // "mode".  Its kernels are instantiated in a translation unit of its own
 // (tgv_mode_<m>.cu) so the modes compile in parallel; the C ABI dispatches
-// through the table returned by mode_table().
+// through the table returned by mode_launchers().
 #pragma once
 
 #include "tgv_common.cuh"
@@ -26,49 +26,61 @@ constexpr ModeKey MODE_KEYS[NUM_MODES] = {
     {TGV_F32, TGV_F16, TGV_F32, TGV_F32},    // 7 Q FP32, Qt FP16
 };
 
-// Tile shapes (TX, TY); tile id t is 1-based in the C ABI.
+// Tile shapes (TX, TY) and points per thread; tile id t is 1-based in the C
+// ABI.  FP32/FP16 compute uses two x points per thread; FP64 compute one, on
+// smaller tiles (an FP64 ring of a 32x16 tile would not fit shared memory).
+// A tile whose shared memory exceeds STAGE_SMEM_LIMIT for a mode's storage
+// types is not used for that mode.
 constexpr int NUM_TILES = 3;
 constexpr int TILE_TX[NUM_TILES] = {32, 16, 16};
-constexpr int TILE_TY[NUM_TILES] = {8, 16, 8};
+constexpr int TILE_TY[NUM_TILES] = {16, 16, 8};
+constexpr int TILE_TX_F64[NUM_TILES] = {16, 16, 8};
+constexpr int TILE_TY_F64[NUM_TILES] = {8, 8, 8};
+
+inline int tile_tx(int comp, int t) { return comp == TGV_F64 ? TILE_TX_F64[t] : TILE_TX[t]; }
+inline int tile_ty(int comp, int t) { return comp == TGV_F64 ? TILE_TY_F64[t] : TILE_TY[t]; }
 
 using StageFn = cudaError_t (*)(const Problem&, const StageArgs&, int zchunk, cudaStream_t);
-using SmemFn = size_t (*)();
 using OccFn = int (*)();
 using InitFn = cudaError_t (*)(const Problem&, void*, cudaStream_t);
 using DiagFn = cudaError_t (*)(const Problem&, const void*, double*, int, cudaStream_t);
 
 struct ModeLaunchers {
-  StageFn stage[NUM_TILES];   // EPI_RK
-  StageFn rhs[NUM_TILES];     // EPI_RHS
-  SmemFn smem[NUM_TILES];
-  OccFn occupancy[NUM_TILES]; // resident CTAs per SM of the EPI_RK kernel
+  StageFn stage[NUM_TILES];      // EPI_RK
+  StageFn stage_diag[NUM_TILES]; // EPI_RK with the fused diagnostics of its input
+  StageFn rhs[NUM_TILES];        // EPI_RHS
+  OccFn occupancy[NUM_TILES];    // resident CTAs per SM of the EPI_RK kernel
+  size_t smem[NUM_TILES];        // dynamic shared memory per CTA
   InitFn init;
   DiagFn diag_partial;
 };
 
 const ModeLaunchers& mode_launchers(int mode);
 
-template <class TS, class TT, class TC, class TA, int TX, int TY, int EPI>
+template <class TS, class TT, class TC, class TA, int TX, int TY, int NP, int EPI, bool DIAG>
 cudaError_t launch_stage(const Problem& P, const StageArgs& S, int zchunk, cudaStream_t st) {
-  auto kern = stage_kernel<TS, TT, TC, TA, TX, TY, EPI>;
-  const size_t smem = stage_smem_bytes<TC, TX, TY>();
+  auto kern = stage_kernel<TS, TT, TC, TA, TX, TY, NP, EPI, DIAG>;
+  const size_t smem = stage_smem_bytes<TS, TT, TC, TX, TY, NP>();
+  if (smem > STAGE_SMEM_LIMIT) return cudaErrorInvalidConfiguration;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   const int n = P.n;
   dim3 grid((n + TX - 1) / TX, (n + TY - 1) / TY, (n + zchunk - 1) / zchunk);
-  dim3 block(TX, TY);
+  dim3 block(TX / NP, TY);
   kern<<<grid, block, smem, st>>>(P, S);
   return cudaGetLastError();
 }
 
-template <class TS, class TT, class TC, class TA, int TX, int TY>
+template <class TS, class TT, class TC, class TA, int TX, int TY, int NP>
 int stage_occupancy() {
-  auto kern = stage_kernel<TS, TT, TC, TA, TX, TY, EPI_RK>;
-  const size_t smem = stage_smem_bytes<TC, TX, TY>();
+  auto kern = stage_kernel<TS, TT, TC, TA, TX, TY, NP, EPI_RK, false>;
+  const size_t smem = stage_smem_bytes<TS, TT, TC, TX, TY, NP>();
+  if (smem > STAGE_SMEM_LIMIT) return 0;
   if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
     return 0;
   int nb = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kern, TX * TY, smem) != cudaSuccess) return 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kern, (TX / NP) * TY, smem) != cudaSuccess)
+    return 0;
   return nb;
 }
 
@@ -82,30 +94,37 @@ cudaError_t launch_init(const Problem& P, void* q, cudaStream_t st) {
   return cudaGetLastError();
 }
 
-template <class TS>
+template <class TS, class TC>
 cudaError_t launch_diag_partial(const Problem& P, const void* q, double* part, int nblocks,
                                 cudaStream_t st) {
-  diag_partial_kernel<TS><<<nblocks, DIAG_THREADS, 0, st>>>(P, static_cast<const TS*>(q), part);
+  diag_partial_kernel<TS, TC><<<nblocks, dim3(DIAG_TX, DIAG_TY), 0, st>>>(
+      P, static_cast<const TS*>(q), part);
   return cudaGetLastError();
+}
+
+template <class TS, class TT, class TC, class TA, int TX, int TY, int NP>
+void set_tile(ModeLaunchers& L, int t) {
+  L.stage[t] = launch_stage<TS, TT, TC, TA, TX, TY, NP, EPI_RK, false>;
+  L.stage_diag[t] = launch_stage<TS, TT, TC, TA, TX, TY, NP, EPI_RK, true>;
+  L.rhs[t] = launch_stage<TS, TT, TC, TA, TX, TY, NP, EPI_RHS, false>;
+  L.occupancy[t] = stage_occupancy<TS, TT, TC, TA, TX, TY, NP>;
+  L.smem[t] = stage_smem_bytes<TS, TT, TC, TX, TY, NP>();
 }
 
 template <class TS, class TT, class TC, class TA>
 ModeLaunchers make_launchers() {
   ModeLaunchers L;
-  L.stage[0] = launch_stage<TS, TT, TC, TA, 32, 8, EPI_RK>;
-  L.stage[1] = launch_stage<TS, TT, TC, TA, 16, 16, EPI_RK>;
-  L.stage[2] = launch_stage<TS, TT, TC, TA, 16, 8, EPI_RK>;
-  L.rhs[0] = launch_stage<TS, TT, TC, TA, 32, 8, EPI_RHS>;
-  L.rhs[1] = launch_stage<TS, TT, TC, TA, 16, 16, EPI_RHS>;
-  L.rhs[2] = launch_stage<TS, TT, TC, TA, 16, 8, EPI_RHS>;
-  L.smem[0] = stage_smem_bytes<TC, 32, 8>;
-  L.smem[1] = stage_smem_bytes<TC, 16, 16>;
-  L.smem[2] = stage_smem_bytes<TC, 16, 8>;
-  L.occupancy[0] = stage_occupancy<TS, TT, TC, TA, 32, 8>;
-  L.occupancy[1] = stage_occupancy<TS, TT, TC, TA, 16, 16>;
-  L.occupancy[2] = stage_occupancy<TS, TT, TC, TA, 16, 8>;
+  if constexpr (std::is_same<TC, double>::value) {
+    set_tile<TS, TT, TC, TA, TILE_TX_F64[0], TILE_TY_F64[0], 1>(L, 0);
+    set_tile<TS, TT, TC, TA, TILE_TX_F64[1], TILE_TY_F64[1], 1>(L, 1);
+    set_tile<TS, TT, TC, TA, TILE_TX_F64[2], TILE_TY_F64[2], 1>(L, 2);
+  } else {
+    set_tile<TS, TT, TC, TA, TILE_TX[0], TILE_TY[0], 2>(L, 0);
+    set_tile<TS, TT, TC, TA, TILE_TX[1], TILE_TY[1], 2>(L, 1);
+    set_tile<TS, TT, TC, TA, TILE_TX[2], TILE_TY[2], 2>(L, 2);
+  }
   L.init = launch_init<TS>;
-  L.diag_partial = launch_diag_partial<TS>;
+  L.diag_partial = launch_diag_partial<TS, TC>;
   return L;
 }
 

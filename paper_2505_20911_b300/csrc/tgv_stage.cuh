@@ -4,33 +4,40 @@
 // equations (4th-order central differences, Blaisdell split convective terms,
 // Sec. 2.3.1) at every grid point and folds the RK update of Sec. 3.1,
 // Eqs. 3-4, into its epilogue:  Qt <- A Qt + dt R,  Q_out <- Q_in + B Qt.
-// With EPI_RHS it writes R instead.
+// With EPI_RHS it writes R instead.  With DIAG it also reduces the
+// diagnostics of Sec. 4.1, Eqs. 11-12 of its input state.
 //
-// Discretisation (the same discrete operator the FP64 oracle defines):
-//   D f   = (-f[+2] + 8 f[+1] - 8 f[-1] + f[-2]) / 12h
-//   D2 f  = (-f[+2] + 16 f[+1] - 30 f[0] + 16 f[-1] - f[-2]) / 12h^2
-//   C_phi = 1/2 sum_j [D_j(u_j f) + u_j D_j f + f D_j u_j]      (Blaisdell; f = rho phi)
-//   momentum i viscous = nu [sum_j D2_j u_i + 1/3 D2_i u_i + 1/3 D_i s_i],
-//                        s_i = sum_{k != i} D_k u_k
-//   energy   = -C_E - sum_j D_j(p u_j) + sum_j D2_j H_j
-//              + nu [2 sum_{i<j} D_i D_j(u_i u_j) - 5/3 sum_j D_j(u_j s_j)],
-//              H_j = kappa T + nu (|u|^2/2 + u_j^2/6)
-//   (the viscous work d(u_i tau_ij)/dx_j and the heat flux rewritten exactly
-//   in telescoping form, so mass, momentum and total energy are conserved to
-//   round-off).
+// Discrete operator (identical to the FP64 oracle's, up to rounding order):
+//   D f  = (-f[+2] + 8 f[+1] - 8 f[-1] + f[-2]) / 12h
+//   D2 f = (-f[+2] + 16 f[+1] - 30 f[0] + 16 f[-1] - f[-2]) / 12h^2
+//   C_c  = a sum_j D_j(u_j f_c) + b [sum_j u_j D_j f_c + f_c div u]
+//          (Blaisdell: a = b = 1/2;  divergence form: a = 1, b = 0)
+//   R_rho   = -C_rho
+//   R_m(i)  = -C_m(i) - D_i p + nu [sum_j (1 + delta_ij/3) D2_j u_i + 1/3 D_i s_i]
+//   R_E     = -C_E - sum_j D_j(p u_j) + sum_j D2_j H_j
+//             + nu [2 sum_{i<j} D_i D_j(u_i u_j) - 5/3 sum_j D_j(u_j s_j)]
+//   s_i = sum_{k != i} D_k u_k,  H_j = kappa T + nu (|u|^2/2 + u_j^2/6).
+// The pressure terms are merged with the convective fluxes of the same
+// direction: a D_j(u_j rho u_j) + D_j p = D_j(a u_j rho u_j + p) and
+// a D_j(u_j rho E) + D_j(p u_j) = D_j(u_j (a rho E + p)) (linearity of D).
 //
-// Work decomposition (B300): a CTA owns a TX x TY column tile and marches in z
-// over `zchunk` planes.  Each z plane of the tile plus a 2-point halo is read
-// once from HBM (periodic wrap), converted to the compute type, and turned into
-// primitives in a 5-plane shared-memory ring; every stencil tap afterwards is
-// a shared-memory read.  Per plane:
-//   load   : plane z+2 -> ring (conserved, u, v, w, p, T); sync
-//   grads  : D_x u, D_y v of plane z+2 on the halo strips that need them;
-//            centre plane z: D_z w, D_y(uv), D_z(uw), D_z(vw) on strips; sync
-//   output : all terms at plane z for the TX x TY points, RK epilogue; sync
+// B300 work decomposition.  A CTA owns a TX x TY column tile and marches in z
+// over `zchunk` planes; each thread owns NP consecutive x points (a "unit";
+// NP = 2 pairs the FP32 arithmetic into f32x2 instructions and the shared
+// loads into 64-bit accesses).  Each z plane of the tile plus a 2-point halo
+// is read once from HBM (periodic wrap; the next plane is prefetched into
+// registers while the current one is computed), converted to the compute
+// type, and turned into primitives in a 6-plane shared-memory ring.  Per
+// plane, with two CTA barriers:
+//   1. primitives of the prefetched plane zl -> ring slot            | barrier
+//   2. prefetch plane zl+1; D_x u + D_y v of plane zl (z-taps of s_z);
+//      centre plane k = zl-2: s_x, s_y and the mixed-derivative fields on
+//      the tile and its x/y halo strips (double-buffered)              | barrier
+//   3. every term at plane k for the thread's unit, RK epilogue.
 #pragma once
 
 #include "tgv_common.cuh"
+#include "tgv_vec.cuh"
 
 namespace tgv {
 
@@ -41,286 +48,508 @@ struct StageArgs {
   void* q_out;        // Q layout, TS (EPI_RK)
   void* qt;           // Q layout, TT (EPI_RK)
   void* r_out;        // Q layout, TC (EPI_RHS)
+  double* diag_part;  // [gridDim.x*gridDim.y*gridDim.z][TGV_DIAG_COUNT] (DIAG)
   double a, b, dt;    // A_i, B_i, dt
   int read_qt;        // 0 when A_i == 0
   int write_qt;       // 0 on the last substep
   int zchunk;         // z planes per CTA
 };
 
-// Shared-memory fields of a ring plane.
-enum { F_RHO = 0, F_RU, F_RV, F_RW, F_RE, F_U, F_V, F_W, F_P, F_T, F_DXU, F_DYV, NF };
-// Per-centre-plane strip fields.
-enum { S_DZW = 0, S_EYUV, S_EZUW, S_EZVW, NS };
+// Ring-plane fields (compute type).
+enum { F_RHO = 0, F_RU, F_RV, F_RW, F_RE, F_U, F_V, F_W, F_P, F_H0, NFLD };
+// Strip fields of the centre plane.
+enum { S_SX = 0, S_SY, S_GX, S_GY, NSTRIP };
+// Ring depth: planes k-2..k+2 are read while the next plane is committed
+// before the first barrier, so the primitives ring needs 6 slots; the s_z
+// ring is written only after that barrier and needs 5.
+constexpr int NSLOT = 6;
+constexpr int NSZ = 5;
 
-template <int TX, int TY>
-struct Tile {
-  static constexpr int RX = TX + 4, RY = TY + 4, PL = RX * RY, NT = TX * TY;
-  static constexpr int PER = (PL + NT - 1) / NT;
+template <int TX, int TY, int NP>
+struct Geo {
+  static_assert(TX % NP == 0, "tile width must be a multiple of the unit");
+  static constexpr int TXU = TX / NP;       // threads per tile row
+  static constexpr int NT = TXU * TY;       // threads per CTA
+  static constexpr int RX = TX + 4, RY = TY + 4, PL = RX * RY;
+  static constexpr int RXU = RX / NP;       // units per halo-region row
+  static constexpr int PLU = RXU * RY;      // units in the halo region
+  static constexpr int PERU = (PLU + NT - 1) / NT;  // region units per thread
+  static constexpr int HALO_UNITS = PLU - NT;        // region units outside the tile
+  static constexpr int HXU = 2 * (2 / NP) * TY;  // x-halo strip units (both sides)
+  static constexpr int HYU = 4 * TXU;            // y-halo strip units (both sides)
+  static constexpr int HU = HXU + HYU;
+  static constexpr int PERH = (HU + NT - 1) / NT;
 };
 
-template <class TC, int TX, int TY>
+// Shared memory: ring, s_z ring, strips (compute type), then the cp.async
+// staging of one raw plane (storage type) and two raw Qt planes of the tile.
+template <class TS, class TT, class TC, int TX, int TY, int NP>
 constexpr size_t stage_smem_bytes() {
-  return (size_t)(5 * NF + NS) * Tile<TX, TY>::PL * sizeof(TC);
+  using G = Geo<TX, TY, NP>;
+  return sizeof(TC) * ((size_t)NSLOT * NFLD * G::PL + (size_t)NSZ * TX * TY +
+                       (size_t)NSTRIP * G::PL) +
+         sizeof(TS) * NP * 5 * (size_t)G::PLU + sizeof(TT) * NP * 2 * 5 * (size_t)G::NT;
+}
+// Largest dynamic shared memory a stage CTA may request (B300: 227 KB per CTA,
+// less the static reduction buffer of the fused-diagnostics variant).
+constexpr size_t STAGE_SMEM_LIMIT = 232448 - 2048;
+
+// Asynchronous global -> shared copies of 4 or 8 bytes (one unit).
+template <int BYTES>
+__device__ __forceinline__ void cp_async(void* smem_dst, const void* gmem_src) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(smem_dst);
+  if constexpr (BYTES == 16)
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(d), "l"(gmem_src) : "memory");
+  else
+    asm volatile("cp.async.ca.shared.global [%0], [%1], %2;" ::"r"(d), "l"(gmem_src), "n"(BYTES)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N> __device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
 }
 
-template <class TS, class TT, class TC, class TA, int TX, int TY, int EPI>
-__global__ void __launch_bounds__(TX * TY)
+template <class V> struct Taps { V m2, m1, p1, p2; };
+
+template <class V> __device__ __forceinline__ V dsum(const Taps<V>& t, V c8) {
+  return fma(c8, t.p1 - t.m1, t.m2 - t.p2);  // 8(f+1 - f-1) - (f+2 - f-2)
+}
+template <class V> __device__ __forceinline__ V d2sum(const Taps<V>& t, V c, V c16, V cm30) {
+  return fma(c16, t.p1 + t.m1, fma(cm30, c, -(t.p2 + t.m2)));
+}
+template <class V> __device__ __forceinline__ Taps<V> tmul(const Taps<V>& a, const Taps<V>& b) {
+  return {a.m2 * b.m2, a.m1 * b.m1, a.p1 * b.p1, a.p2 * b.p2};
+}
+template <class V> __device__ __forceinline__ Taps<V> tfma(const Taps<V>& a, const Taps<V>& b,
+                                                           const Taps<V>& c) {
+  return {fma(a.m2, b.m2, c.m2), fma(a.m1, b.m1, c.m1), fma(a.p1, b.p1, c.p1), fma(a.p2, b.p2, c.p2)};
+}
+template <class V> __device__ __forceinline__ Taps<V> tscale(V s, const Taps<V>& a) {
+  return {s * a.m2, s * a.m1, s * a.p1, s * a.p2};
+}
+template <class V> __device__ __forceinline__ Taps<V> taxpy(V s, const Taps<V>& a, const Taps<V>& c) {
+  return {fma(s, a.m2, c.m2), fma(s, a.m1, c.m1), fma(s, a.p1, c.p1), fma(s, a.p2, c.p2)};
+}
+
+template <class T> __device__ __forceinline__ T warp_sum(T v) {
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+  return v;
+}
+
+template <class TS, class TT, class TC, class TA, int TX, int TY, int NP, int EPI, bool DIAG>
+__global__ void __launch_bounds__(Geo<TX, TY, NP>::NT, 1)
 stage_kernel(const Problem P, const StageArgs S) {
-  using TL = Tile<TX, TY>;
-  constexpr int RX = TL::RX, PL = TL::PL, NT = TL::NT, PER = TL::PER;
+  using G = Geo<TX, TY, NP>;
+  using V = Vec<TC, NP>;
+  using IO = UnitIO<TC, NP, TS>;
+  constexpr int RX = G::RX, PL = G::PL, NT = G::NT, RXU = G::RXU, PLU = G::PLU;
+  constexpr int PERU = G::PERU, TXU = G::TXU;
+
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  TC* ring = reinterpret_cast<TC*>(smem_raw);  // [5][NF][PL]
-  TC* scr = ring + 5 * NF * PL;                // [NS][PL]
+  TC* ring = reinterpret_cast<TC*>(smem_raw);         // [NSLOT][NFLD][PL]
+  TC* szr = ring + NSLOT * NFLD * PL;                  // [NSZ][TX*TY]
+  TC* strips = szr + NSZ * TX * TY;                    // [NSTRIP][PL]
 
   const int n = P.n;
   const long long nn = (long long)n * n, n3 = nn * n;
-  const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * TX + tx;
+  const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * TXU + tx;
   const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
   const int z0 = blockIdx.z * S.zchunk;
   const int z1 = min(z0 + S.zchunk, n);
   const TS* __restrict__ q_in = static_cast<const TS*>(S.q_in);
 
-  const TC c_inv12h = cvt<TC>(P.inv12h), c_inv12h2 = cvt<TC>(P.inv12h2);
-  const TC c_gm1 = cvt<TC>(P.gm1), c_gM2 = cvt<TC>(P.gM2);
-  const TC c_nu = cvt<TC>(P.nu), c_kappa = cvt<TC>(P.kappa);
-  const TC c_rho0 = cvt<TC>(P.rho0), c_rhoE0 = cvt<TC>(P.rhoE0);
-  const TC c_half = cvt<TC>(0.5), c_sixth = cvt<TC>(1.0 / 6.0), c_third = cvt<TC>(1.0 / 3.0);
-  const TC c_8 = cvt<TC>(8.0), c_16 = cvt<TC>(16.0), c_30 = cvt<TC>(30.0);
-  const TC c_2 = cvt<TC>(2.0), c_53 = cvt<TC>(5.0 / 3.0), c_zero = cvt<TC>(0.0);
+  const V c_inv12h = V::splat(cvt<TC>(P.inv12h)), c_inv12h2 = V::splat(cvt<TC>(P.inv12h2));
+  const V c_gm1 = V::splat(cvt<TC>(P.gm1)), c_gM2 = V::splat(cvt<TC>(P.gM2));
+  const V c_nu = V::splat(cvt<TC>(P.nu)), c_kappa = V::splat(cvt<TC>(P.kappa));
+  const V c_rho0 = V::splat(cvt<TC>(P.rho0)), c_rhoE0 = V::splat(cvt<TC>(P.rhoE0));
+  const V c_half = V::splat(cvt<TC>(0.5)), c_nu6 = V::splat(cvt<TC>(P.nu / 6.0));
+  const V c_nuh = V::splat(cvt<TC>(0.5 * P.nu));
+  const V c_8 = V::splat(cvt<TC>(8.0)), c_16 = V::splat(cvt<TC>(16.0));
+  const V c_m30 = V::splat(cvt<TC>(-30.0)), c_2 = V::splat(cvt<TC>(2.0));
+  const V c_43 = V::splat(cvt<TC>(4.0 / 3.0)), c_13 = V::splat(cvt<TC>(1.0 / 3.0));
+  const V c_m53 = V::splat(cvt<TC>(-5.0 / 3.0)), c_one = V::splat(cvt<TC>(1.0));
   const bool blaisdell = (P.split == TGV_SPLIT_BLAISDELL);
+  const V c_alpha = V::splat(cvt<TC>(blaisdell ? 0.5 : 1.0));
+  const V c_beta = V::splat(cvt<TC>(blaisdell ? 0.5 : 0.0));
 
-  // In-plane global offsets of the halo-region points this thread loads.
-  int roff[PER];
+  // ---- region units this thread loads and converts each plane.  Unit q < NT
+  // is thread q's own tile unit; units q >= NT are the halo (rows 0-1, the
+  // left/right columns of rows 2..TY+1, rows TY+2..TY+3).
+  using RawS = typename UnitIO<TC, NP, TS>::Raw;
+  using RawT = typename UnitIO<TA, NP, TT>::Raw;
+  RawS* stage_q = reinterpret_cast<RawS*>(strips + NSTRIP * PL);       // [5][PLU]
+  RawT* stage_t = reinterpret_cast<RawT*>(stage_q + 5 * PLU);         // [2][5][NT]
+  int goff[PERU], eoff[PERU];
 #pragma unroll
-  for (int r = 0; r < PER; ++r) {
-    const int idx = tid + r * NT;
-    roff[r] = -1;
-    if (idx < PL) {
-      int gx = (x0 - 2 + idx % RX) % n;
-      if (gx < 0) gx += n;
-      int gy = (y0 - 2 + idx / RX) % n;
-      if (gy < 0) gy += n;
-      roff[r] = gy * n + gx;
+  for (int r = 0; r < PERU; ++r) {
+    const int q = tid + r * NT;
+    goff[r] = -1;
+    eoff[r] = 0;
+    if (q < PLU) {
+      int rx, ry;
+      if (q < NT) {
+        rx = 2 + NP * (q % TXU);
+        ry = 2 + q / TXU;
+      } else {
+        int h = q - NT;
+        constexpr int side = 2 / NP;  // units per row on each side
+        if (h < 2 * RXU) { ry = h / RXU; rx = (h % RXU) * NP; }
+        else if ((h -= 2 * RXU) < TY * 2 * side) {
+          ry = 2 + h / (2 * side);
+          const int qq = h % (2 * side);
+          rx = qq < side ? qq * NP : TX + 2 + (qq - side) * NP;
+        } else {
+          h -= TY * 2 * side;
+          ry = TY + 2 + h / RXU;
+          rx = (h % RXU) * NP;
+        }
+      }
+      int gx = x0 - 2 + rx;
+      gx = gx < 0 ? gx + n : (gx >= n ? gx % n : gx);
+      int gy = y0 - 2 + ry;
+      gy = gy < 0 ? gy + n : (gy >= n ? gy % n : gy);
+      goff[r] = gy * n + gx;
+      eoff[r] = ry * RX + rx;
     }
   }
-
-  auto D = [&](TC fm2, TC fm1, TC fp1, TC fp2) -> TC {  // raw first-derivative sum
-    return c_8 * (fp1 - fm1) - (fp2 - fm2);
+  const long long tile_off = (long long)(y0 + ty) * n + (x0 + NP * tx);
+  const bool active_xy = (x0 + NP * tx < n) && (y0 + ty < n);
+  auto prefetch = [&](int zl) {  // cp.async of raw plane zl into the staging
+    int zw = zl % n;
+    if (zw < 0) zw += n;
+    const long long zoff = (long long)zw * nn;
+#pragma unroll
+    for (int r = 0; r < PERU; ++r) {
+      if (goff[r] >= 0) {
+        const int q = tid + r * NT;
+#pragma unroll
+        for (int c = 0; c < 5; ++c)
+          cp_async<sizeof(RawS)>(stage_q + c * PLU + q, q_in + zoff + goff[r] + c * n3);
+      }
+    }
+  };
+  auto prefetch_qt = [&](int kq) {  // cp.async of this unit's Qt at plane kq
+    if (!active_xy) return;
+    const TT* qt = static_cast<const TT*>(S.qt);
+    RawT* dst = stage_t + (kq & 1) * 5 * NT;
+#pragma unroll
+    for (int c = 0; c < 5; ++c)
+      cp_async<sizeof(RawT)>(dst + c * NT + tid, qt + (long long)kq * nn + tile_off + c * n3);
+  };
+  RawS qin_q[3][5];  // raw Q of the own unit at planes zl, zl-1, zl-2
+  auto commit = [&](int slot) {  // staged raw plane -> primitives in the ring
+    TC* base = ring + slot * NFLD * PL;
+#pragma unroll
+    for (int r = 0; r < PERU; ++r) {
+      const int q = tid + r * NT;
+      if (q < PLU) {
+        RawS raw[5];
+#pragma unroll
+        for (int c = 0; c < 5; ++c) raw[c] = stage_q[c * PLU + q];
+        if (r == 0) {
+#pragma unroll
+          for (int c = 0; c < 5; ++c) {
+            qin_q[2][c] = qin_q[1][c];
+            qin_q[1][c] = qin_q[0][c];
+            qin_q[0][c] = raw[c];
+          }
+        }
+        const int e = eoff[r];
+        const V rho = IO::conv(raw[0]) + c_rho0;
+        const V ru = IO::conv(raw[1]), rv = IO::conv(raw[2]), rw = IO::conv(raw[3]);
+        const V rE = IO::conv(raw[4]) + c_rhoE0;
+        const V ri = rcp(rho);
+        const V uu = ru * ri, vv = rv * ri, ww = rw * ri;
+        const V ke = c_half * fma(ru, uu, fma(rv, vv, rw * ww));
+        const V p = c_gm1 * (rE - ke);
+        const V T = c_gM2 * p * ri;
+        const V h0 = fma(c_kappa, T, c_nuh * fma(uu, uu, fma(vv, vv, ww * ww)));
+        rho.store(base + F_RHO * PL + e);
+        ru.store(base + F_RU * PL + e);
+        rv.store(base + F_RV * PL + e);
+        rw.store(base + F_RW * PL + e);
+        rE.store(base + F_RE * PL + e);
+        uu.store(base + F_U * PL + e);
+        vv.store(base + F_V * PL + e);
+        ww.store(base + F_W * PL + e);
+        p.store(base + F_P * PL + e);
+        h0.store(base + F_H0 * PL + e);
+      }
+    }
   };
 
+  // tap loaders on a plane-layout array f (offsets of the unit at e)
+  auto xt = [&](const TC* f, int e, V& ctr) -> Taps<V> {
+    if constexpr (NP == 1) {
+      ctr = V::load(f + e);
+      return {V::load(f + e - 2), V::load(f + e - 1), V::load(f + e + 1), V::load(f + e + 2)};
+    } else {
+      const V A = V::load(f + e - 2), B = V::load(f + e), C = V::load(f + e + 2);
+      ctr = B;
+      return {A, V::mix(A, B), V::mix(B, C), C};
+    }
+  };
+  auto yt = [&](const TC* f, int e) -> Taps<V> {
+    return {V::load(f + e - 2 * RX), V::load(f + e - RX), V::load(f + e + RX), V::load(f + e + 2 * RX)};
+  };
+
+  // diagnostics accumulators (per thread, FP64; per-point values are formed in
+  // the compute type, the NP lanes of a unit summed, then added in FP64)
+  double dacc[TGV_DIAG_COUNT];
+  if constexpr (DIAG) {
+#pragma unroll
+    for (int m = 0; m < TGV_DIAG_COUNT; ++m) dacc[m] = 0.0;
+  }
+
   const int zbase = z0 - 2;
-  for (int zl = z0 - 2; zl < z1 + 2; ++zl) {
-    // ---------------------------------------------------------- load plane zl
-    const int slot = (zl - zbase) % 5;
-    {
-      int zw = zl % n;
-      if (zw < 0) zw += n;
-      const long long zoff = (long long)zw * nn;
-      TC* base = ring + slot * NF * PL;
+  const int rxc = 2 + NP * tx, ryc = 2 + ty;
+  const int ec = ryc * RX + rxc;        // unit centre in plane layout
+  const int et = ty * TX + NP * tx;     // unit in tile layout (s_z ring)
+
+  prefetch(zbase);
+  cp_async_commit();
+  for (int zl = zbase; zl < z1 + 2; ++zl) {
+    const int slot = (zl - zbase) % NSLOT;
+    cp_async_wait<0>();
+    commit(slot);
+    __syncthreads();
+    // next plane and, for the next centre plane, this unit's Qt (one group)
+    if (zl + 1 < z1 + 2) prefetch(zl + 1);
+    if (EPI == EPI_RK && S.read_qt && zl - 1 >= z0 && zl - 1 < z1) prefetch_qt(zl - 1);
+    cp_async_commit();
+
+    const int k = zl - 2;
+    const TC* pk[5];  // ring planes k-2 .. k+2
 #pragma unroll
-      for (int r = 0; r < PER; ++r) {
-        const int idx = tid + r * NT;
-        if (idx < PL) {
-          const long long o = zoff + roff[r];
-          const TC rho = cvt<TC>(q_in[o]) + c_rho0;
-          const TC ru = cvt<TC>(q_in[o + n3]);
-          const TC rv = cvt<TC>(q_in[o + 2 * n3]);
-          const TC rw = cvt<TC>(q_in[o + 3 * n3]);
-          const TC rE = cvt<TC>(q_in[o + 4 * n3]) + c_rhoE0;
-          const TC ri = recip(rho);
-          const TC u = ru * ri, v = rv * ri, w = rw * ri;
-          const TC ke = c_half * (ru * u + rv * v + rw * w);
-          const TC p = c_gm1 * (rE - ke);
-          base[F_RHO * PL + idx] = rho;
-          base[F_RU * PL + idx] = ru;
-          base[F_RV * PL + idx] = rv;
-          base[F_RW * PL + idx] = rw;
-          base[F_RE * PL + idx] = rE;
-          base[F_U * PL + idx] = u;
-          base[F_V * PL + idx] = v;
-          base[F_W * PL + idx] = w;
-          base[F_P * PL + idx] = p;
-          base[F_T * PL + idx] = c_gM2 * p * ri;
+    for (int d = 0; d < 5; ++d) pk[d] = ring + ((zl - 4 + d - zbase + 2 * NSLOT) % NSLOT) * NFLD * PL;
+    const TC* szk[5];
+#pragma unroll
+    for (int d = 0; d < 5; ++d) szk[d] = szr + ((zl - 4 + d - zbase + 2 * NSZ) % NSZ) * TX * TY;
+    TC* st = strips;
+
+    // ---- phase A: s_z taps of plane zl; centre-plane strip fields
+    {
+      const TC* pl = ring + slot * NFLD * PL;
+      V cdummy;
+      const V dxu = dsum(xt(pl + F_U * PL, ec, cdummy), c_8);
+      const V dyv = dsum(yt(pl + F_V * PL, ec), c_8);
+      (c_inv12h * (dxu + dyv)).store(szr + ((zl - zbase) % NSZ) * TX * TY + et);
+    }
+    V div = V::splat(cvt<TC>(0.0));
+    if (k >= z0) {
+      const TC* P0 = pk[2];
+      auto ztw = [&](int fld, int e) -> Taps<V> {
+        return {V::load(pk[0] + fld * PL + e), V::load(pk[1] + fld * PL + e),
+                V::load(pk[3] + fld * PL + e), V::load(pk[4] + fld * PL + e)};
+      };
+      // own unit (tile point): everything
+      {
+        V uc;
+        const Taps<V> ux = xt(P0 + F_U * PL, ec, uc);
+        const Taps<V> uy = yt(P0 + F_U * PL, ec), vy = yt(P0 + F_V * PL, ec);
+        const Taps<V> uz = ztw(F_U, ec), vz = ztw(F_V, ec), wz = ztw(F_W, ec);
+        const V dxu = c_inv12h * dsum(ux, c_8);
+        const V dyv = c_inv12h * dsum(vy, c_8);
+        const V dzw = c_inv12h * dsum(wz, c_8);
+        div = dxu + dyv + dzw;
+        (dyv + dzw).store(st + S_SX * PL + ec);
+        (dxu + dzw).store(st + S_SY * PL + ec);
+        const V eyuv = dsum(tmul(uy, vy), c_8);
+        const V ezuw = dsum(tmul(uz, wz), c_8);
+        const V ezvw = dsum(tmul(vz, wz), c_8);
+        (c_2 * c_inv12h * (eyuv + ezuw)).store(st + S_GX * PL + ec);
+        (c_2 * c_inv12h * ezvw).store(st + S_GY * PL + ec);
+      }
+      // halo strips: x-halo units need s_x and G_x, y-halo units s_y and G_y
+#pragma unroll
+      for (int r = 0; r < G::PERH; ++r) {
+        const int h = tid + r * NT;
+        if (h < G::HXU) {
+          constexpr int per_side = 2 / NP;
+          const int row = h / (2 * per_side), q = h % (2 * per_side);
+          const int rx = q < per_side ? q * NP : TX + 2 + (q - per_side) * NP;
+          const int e = (2 + row) * RX + rx;
+          const V dyv = c_inv12h * dsum(yt(P0 + F_V * PL, e), c_8);
+          const Taps<V> wz = ztw(F_W, e);
+          const V dzw = c_inv12h * dsum(wz, c_8);
+          (dyv + dzw).store(st + S_SX * PL + e);
+          const V eyuv = dsum(tmul(yt(P0 + F_U * PL, e), yt(P0 + F_V * PL, e)), c_8);
+          const V ezuw = dsum(tmul(ztw(F_U, e), wz), c_8);
+          (c_2 * c_inv12h * (eyuv + ezuw)).store(st + S_GX * PL + e);
+        } else if (h < G::HU) {
+          const int hy = h - G::HXU;
+          const int rowsel = hy / TXU, col = hy % TXU;
+          const int ry = rowsel < 2 ? rowsel : TY + rowsel;  // 0,1,TY+2,TY+3
+          const int e = ry * RX + 2 + col * NP;
+          V cd;
+          const V dxu = c_inv12h * dsum(xt(P0 + F_U * PL, e, cd), c_8);
+          const Taps<V> wz = ztw(F_W, e);
+          const V dzw = c_inv12h * dsum(wz, c_8);
+          (dxu + dzw).store(st + S_SY * PL + e);
+          (c_2 * c_inv12h * dsum(tmul(ztw(F_V, e), wz), c_8)).store(st + S_GY * PL + e);
         }
       }
     }
     __syncthreads();
 
-    const int k = zl - 2;  // centre plane
-    int sl[5];             // ring slots of planes k-2 .. k+2
+    // ---- phase B: all terms at plane k for this thread's unit
+    if (k >= z0 && active_xy) {
+      const TC* P0 = pk[2];
+      V fc[5];
 #pragma unroll
-    for (int d = 0; d < 5; ++d) sl[d] = (zl - 4 + d - zbase + 5) % 5;
-
-    // --------------------------------- in-plane gradients of plane zl; strips
-    {
-      TC* base = ring + slot * NF * PL;
-      const TC* U = base + F_U * PL;
-      const TC* V = base + F_V * PL;
-      for (int idx = tid; idx < PL; idx += NT) {
-        const int rx = idx % RX, ry = idx / RX;
-        if (rx >= 2 && rx < TX + 2)
-          base[F_DXU * PL + idx] = c_inv12h * D(U[idx - 2], U[idx - 1], U[idx + 1], U[idx + 2]);
-        if (ry >= 2 && ry < TY + 2)
-          base[F_DYV * PL + idx] =
-              c_inv12h * D(V[idx - 2 * RX], V[idx - RX], V[idx + RX], V[idx + 2 * RX]);
-      }
-      if (k >= z0) {
-        const TC* P0 = ring + sl[2] * NF * PL;
-        const TC* Pm2 = ring + sl[0] * NF * PL;
-        const TC* Pm1 = ring + sl[1] * NF * PL;
-        const TC* Pp1 = ring + sl[3] * NF * PL;
-        const TC* Pp2 = ring + sl[4] * NF * PL;
-        for (int idx = tid; idx < PL; idx += NT) {
-          const int rx = idx % RX, ry = idx / RX;
-          const bool xrow = (ry >= 2 && ry < TY + 2);  // x-strip (incl. tile)
-          const bool ycol = (rx >= 2 && rx < TX + 2);  // y-strip (incl. tile)
-          if (!(xrow || ycol)) continue;
-          const TC wm2 = Pm2[F_W * PL + idx], wm1 = Pm1[F_W * PL + idx];
-          const TC wp1 = Pp1[F_W * PL + idx], wp2 = Pp2[F_W * PL + idx];
-          scr[S_DZW * PL + idx] = c_inv12h * D(wm2, wm1, wp1, wp2);
-          if (xrow) {
-            const TC* U0 = P0 + F_U * PL;
-            const TC* V0 = P0 + F_V * PL;
-            scr[S_EYUV * PL + idx] = c_inv12h * D(U0[idx - 2 * RX] * V0[idx - 2 * RX],
-                                                  U0[idx - RX] * V0[idx - RX],
-                                                  U0[idx + RX] * V0[idx + RX],
-                                                  U0[idx + 2 * RX] * V0[idx + 2 * RX]);
-            scr[S_EZUW * PL + idx] =
-                c_inv12h * D(Pm2[F_U * PL + idx] * wm2, Pm1[F_U * PL + idx] * wm1,
-                             Pp1[F_U * PL + idx] * wp1, Pp2[F_U * PL + idx] * wp2);
-          }
-          if (ycol) {
-            scr[S_EZVW * PL + idx] =
-                c_inv12h * D(Pm2[F_V * PL + idx] * wm2, Pm1[F_V * PL + idx] * wm1,
-                             Pp1[F_V * PL + idx] * wp1, Pp2[F_V * PL + idx] * wp2);
-          }
-        }
-      }
-    }
-    __syncthreads();
-
-    // ------------------------------------------------------ output at plane k
-    if (k >= z0 && x0 + tx < n && y0 + ty < n) {
-      const int c = (ty + 2) * RX + (tx + 2);
-      const TC* P0 = ring + sl[2] * NF * PL;
-      TC fc[5];
+      for (int c = 0; c < 5; ++c) fc[c] = V::load(P0 + c * PL + ec);
+      const V uc[3] = {V::load(P0 + F_U * PL + ec), V::load(P0 + F_V * PL + ec),
+                       V::load(P0 + F_W * PL + ec)};
+      const V h0c = V::load(P0 + F_H0 * PL + ec);
+      const V zero = V::splat(cvt<TC>(0.0));
+      V suf[5], udf[5], d2u[3], ds[3];
 #pragma unroll
-      for (int f = 0; f < 5; ++f) fc[f] = P0[f * PL + c];
-      const TC uc[3] = {P0[F_U * PL + c], P0[F_V * PL + c], P0[F_W * PL + c]};
-      const TC Tc = P0[F_T * PL + c];
-      const TC ke2c = c_half * (uc[0] * uc[0] + uc[1] * uc[1] + uc[2] * uc[2]);
-
-      TC suf[5], udf[5];
+      for (int c = 0; c < 5; ++c) { suf[c] = zero; udf[c] = zero; }
 #pragma unroll
-      for (int f = 0; f < 5; ++f) { suf[f] = c_zero; udf[f] = c_zero; }
-      TC div_raw = c_zero, dpu = c_zero, d2h = c_zero, dus = c_zero;
-      TC dp[3], ds[3], d2u[3], d2own[3];
-#pragma unroll
-      for (int i = 0; i < 3; ++i) { d2u[i] = c_zero; }
+      for (int i = 0; i < 3; ++i) { d2u[i] = zero; ds[i] = zero; }
+      V d2h = zero, dus = zero;
+      V grad[3][3];  // grad[i][j] = raw D_j u_i (diagnostics)
 
 #pragma unroll
       for (int j = 0; j < 3; ++j) {
-        TC dF[5];
+        auto tap = [&](int fld) -> Taps<V> {
+          if (j == 0) { V cd; return xt(P0 + fld * PL, ec, cd); }
+          if (j == 1) return yt(P0 + fld * PL, ec);
+          return {V::load(pk[0] + fld * PL + ec), V::load(pk[1] + fld * PL + ec),
+                  V::load(pk[3] + fld * PL + ec), V::load(pk[4] + fld * PL + ec)};
+        };
+        const Taps<V> U = tap(F_U + j);
+        const Taps<V> aU = tscale(c_alpha, U);
+        const Taps<V> Pt = tap(F_P);
+        // conserved components: D_j f_c, a D_j(u_j f_c) with merged pressure
 #pragma unroll
-        for (int f = 0; f < 5; ++f) dF[f] = c_zero;
-        TC duj = c_zero, dpj = c_zero, dsj = c_zero, d2own_j = c_zero;
-        TC d2uj[3] = {c_zero, c_zero, c_zero};
-        TC d2hj = c_zero;
-#pragma unroll
-        for (int t = 0; t < 4; ++t) {
-          const int s = (t < 2) ? (t - 2) : (t - 1);       // -2, -1, +1, +2
-          const TC cs = (s == -2) ? cvt<TC>(1.0) : (s == -1) ? -c_8 : (s == 1) ? c_8 : cvt<TC>(-1.0);
-          const TC ds2 = (s == -2 || s == 2) ? cvt<TC>(-1.0) : c_16;
-          const TC* Pl;
-          int e;
-          if (j == 2) { Pl = ring + sl[2 + s] * NF * PL; e = c; }
-          else { Pl = P0; e = c + (j == 0 ? s : s * RX); }
-          TC f[5];
-#pragma unroll
-          for (int q = 0; q < 5; ++q) f[q] = Pl[q * PL + e];
-          const TC uu = Pl[F_U * PL + e], vv = Pl[F_V * PL + e], ww = Pl[F_W * PL + e];
-          const TC uj = (j == 0) ? uu : (j == 1) ? vv : ww;
-          const TC pp = Pl[F_P * PL + e], TT = Pl[F_T * PL + e];
-          TC sj;
-          if (j == 0) sj = P0[F_DYV * PL + e] + scr[S_DZW * PL + e];
-          else if (j == 1) sj = P0[F_DXU * PL + e] + scr[S_DZW * PL + e];
-          else sj = Pl[F_DXU * PL + e] + Pl[F_DYV * PL + e];
-#pragma unroll
-          for (int q = 0; q < 5; ++q) {
-            dF[q] = dF[q] + cs * f[q];
-            suf[q] = suf[q] + cs * (uj * f[q]);
-          }
-          duj = duj + cs * uj;
-          dpj = dpj + cs * pp;
-          dpu = dpu + cs * (pp * uj);
-          d2uj[0] = d2uj[0] + ds2 * uu;
-          d2uj[1] = d2uj[1] + ds2 * vv;
-          d2uj[2] = d2uj[2] + ds2 * ww;
-          const TC H = c_kappa * TT + c_nu * (c_half * (uu * uu + vv * vv + ww * ww) + c_sixth * (uj * uj));
-          d2hj = d2hj + ds2 * H;
-          dsj = dsj + cs * sj;
-          dus = dus + cs * (uj * sj);
+        for (int c = 0; c < 5; ++c) {
+          const Taps<V> F = tap(c);
+          const V dF = dsum(F, c_8);
+          udf[c] = fma(uc[j], dF, udf[c]);
+          if (c == 0) continue;
+          Taps<V> g;
+          if (c == 1 + j) g = tfma(aU, F, Pt);                 // a u_j rho u_j + p
+          else if (c == 4) g = tmul(U, taxpy(c_alpha, F, Pt));  // u_j (a rho E + p)
+          else g = tmul(aU, F);
+          suf[c] = suf[c] + dsum(g, c_8);
+          if (c == 1 + j) suf[0] = fma(c_alpha, dF, suf[0]);  // D_j(rho u_j)
         }
-        // centre tap of the second derivatives
-        const TC Hc = c_kappa * Tc + c_nu * (ke2c + c_sixth * (uc[j] * uc[j]));
-        d2hj = d2hj - c_30 * Hc;
+        // velocity second derivatives (and first derivatives for diagnostics)
 #pragma unroll
-        for (int i = 0; i < 3; ++i) d2u[i] = d2u[i] + (d2uj[i] - c_30 * uc[i]);
-        d2own_j = d2uj[j] - c_30 * uc[j];
-        d2own[j] = d2own_j;
-        d2h = d2h + d2hj;
-        div_raw = div_raw + duj;
-        dp[j] = dpj;
-        ds[j] = dsj;
-#pragma unroll
-        for (int q = 0; q < 5; ++q) udf[q] = udf[q] + uc[j] * dF[q];
+        for (int i = 0; i < 3; ++i) {
+          const Taps<V> Ui = (i == j) ? U : tap(F_U + i);
+          const V w8 = (i == j) ? c_43 : c_one;
+          d2u[i] = fma(w8, d2sum(Ui, uc[i], c_16, c_m30), d2u[i]);
+          if constexpr (DIAG) grad[i][j] = dsum(Ui, c_8);
+        }
+        // heat flux + viscous kinetic-energy flux: D2_j H_j
+        {
+          const Taps<V> H = tfma(tscale(c_nu6, U), U, tap(F_H0));
+          const V Hc = fma(c_nu6 * uc[j], uc[j], h0c);
+          d2h = d2h + d2sum(H, Hc, c_16, c_m30);
+        }
+        // dilatation cross terms: D_j s_j and D_j(u_j s_j)
+        {
+          Taps<V> Sj;
+          if (j == 0) { V cd; Sj = xt(st + S_SX * PL, ec, cd); }
+          else if (j == 1) Sj = yt(st + S_SY * PL, ec);
+          else Sj = {V::load(szk[0] + et), V::load(szk[1] + et), V::load(szk[3] + et), V::load(szk[4] + et)};
+          ds[j] = dsum(Sj, c_8);
+          dus = dus + dsum(tmul(U, Sj), c_8);
+        }
+      }
+      // mixed second derivatives: outer D_x of G_x, outer D_y of G_y
+      V gmix;
+      {
+        V cd;
+        gmix = dsum(xt(st + S_GX * PL, ec, cd), c_8) + dsum(yt(st + S_GY * PL, ec), c_8);
       }
 
-      // mixed second derivatives of u_i u_j (outer D over the strip fields)
-      const TC mix =
-          D(scr[S_EYUV * PL + c - 2], scr[S_EYUV * PL + c - 1], scr[S_EYUV * PL + c + 1],
-            scr[S_EYUV * PL + c + 2]) +
-          D(scr[S_EZUW * PL + c - 2], scr[S_EZUW * PL + c - 1], scr[S_EZUW * PL + c + 1],
-            scr[S_EZUW * PL + c + 2]) +
-          D(scr[S_EZVW * PL + c - 2 * RX], scr[S_EZVW * PL + c - RX], scr[S_EZVW * PL + c + RX],
-            scr[S_EZVW * PL + c + 2 * RX]);
-
-      const TC div = c_inv12h * div_raw;
-      TC R[5];
+      V R[5];
 #pragma unroll
-      for (int q = 0; q < 5; ++q) {
-        TC conv;
-        if (blaisdell) conv = c_half * (c_inv12h * (suf[q] + udf[q]) + fc[q] * div);
-        else conv = c_inv12h * suf[q];
-        R[q] = -conv;
-      }
+      for (int c = 0; c < 5; ++c)
+        R[c] = -(fma(c_inv12h, fma(c_beta, udf[c], suf[c]), c_beta * fc[c] * div));
 #pragma unroll
-      for (int i = 0; i < 3; ++i) {
-        const TC visc = c_nu * (c_inv12h2 * (d2u[i] + c_third * d2own[i]) + c_third * c_inv12h * ds[i]);
-        R[1 + i] = R[1 + i] - c_inv12h * dp[i] + visc;
-      }
-      R[4] = R[4] - c_inv12h * dpu + c_inv12h2 * d2h + c_nu * c_inv12h * (c_2 * mix - c_53 * dus);
+      for (int i = 0; i < 3; ++i)
+        R[1 + i] = fma(c_nu, fma(c_inv12h2, d2u[i], c_13 * c_inv12h * ds[i]), R[1 + i]);
+      R[4] = fma(c_inv12h2, d2h, fma(c_nu * c_inv12h, fma(c_m53, dus, gmix), R[4]));
 
-      const long long o = (long long)k * nn + (long long)(y0 + ty) * n + (x0 + tx);
+      if constexpr (DIAG) {
+        // per-point diagnostics of the input state, in the compute type
+        const V wx = c_inv12h * (grad[2][1] - grad[1][2]);
+        const V wy = c_inv12h * (grad[0][2] - grad[2][0]);
+        const V wz = c_inv12h * (grad[1][0] - grad[0][1]);
+        const V ens = fma(wx, wx, fma(wy, wy, wz * wz));
+        const V u2h = c_half * fma(uc[0], uc[0], fma(uc[1], uc[1], uc[2] * uc[2]));
+        const V vals[8] = {u2h, fc[0] * u2h, ens, fc[0], fc[1], fc[2], fc[3], fc[4]};
+        const int slot_of[8] = {0, 1, 2, 4, 5, 6, 7, 8};
+#pragma unroll
+        for (int m = 0; m < 8; ++m) {
+          TC t = vals[m].get(0);
+#pragma unroll
+          for (int e = 1; e < NP; ++e) t = t + vals[m].get(e);
+          dacc[slot_of[m]] += (double)Num<TC>::to_f64(t);
+        }
+        double bad = 0.0;
+#pragma unroll
+        for (int e = 0; e < NP; ++e) {
+          bool ok = true;
+#pragma unroll
+          for (int c = 0; c < 5; ++c) ok = ok && finite_val(fc[c].get(e));
+          bad += ok ? 0.0 : 1.0;
+        }
+        dacc[9] += bad;
+      }
+
+      const long long o = (long long)k * nn + tile_off;
       if constexpr (EPI == EPI_RHS) {
         TC* r_out = static_cast<TC*>(S.r_out);
 #pragma unroll
-        for (int q = 0; q < 5; ++q) r_out[o + q * n3] = R[q];
+        for (int c = 0; c < 5; ++c) R[c].store(r_out + o + c * n3);
       } else {
         TS* q_out = static_cast<TS*>(S.q_out);
         TT* qt = static_cast<TT*>(S.qt);
         const TA a = cvt<TA>(S.a), b = cvt<TA>(S.b), dt = cvt<TA>(S.dt);
 #pragma unroll
-        for (int q = 0; q < 5; ++q) {
-          TA qtn = dt * cvt<TA>(R[q]);
-          if (S.read_qt) qtn = a * cvt<TA>(qt[o + q * n3]) + qtn;
-          const TA qo = cvt<TA>(q_in[o + q * n3]) + b * qtn;
-          q_out[o + q * n3] = cvt<TS>(qo);
-          if (S.write_qt) qt[o + q * n3] = cvt<TT>(qtn);
+        if (S.read_qt) cp_async_wait<1>();  // this plane's Qt group has landed
+        const RawT* qts = stage_t + (k & 1) * 5 * NT;
+#pragma unroll
+        for (int c = 0; c < 5; ++c) {
+          TA qtn[NP], qo[NP], qin[NP], qold[NP];
+          raw_elems<TA, NP>(qin_q[2][c], qin);
+          if (S.read_qt) raw_elems<TA, NP>(qts[c * NT + tid], qold);
+#pragma unroll
+          for (int e = 0; e < NP; ++e) {
+            TA v = dt * cvt<TA>(R[c].get(e));
+            if (S.read_qt) v = a * qold[e] + v;
+            qtn[e] = v;
+            qo[e] = qin[e] + b * v;
+          }
+          UnitStore<TS, NP>::put(q_out + o + c * n3, qo);
+          if (S.write_qt) UnitStore<TT, NP>::put(qt + o + c * n3, qtn);
         }
       }
     }
+  }
+
+  if constexpr (DIAG) {
+    // CTA reduction: warp sums, then a fixed-order pass over warps
+    __shared__ double red[NT / 32 + 1][TGV_DIAG_COUNT];
+    const int lane = tid & 31, warp = tid >> 5;
+#pragma unroll
+    for (int m = 0; m < TGV_DIAG_COUNT; ++m) {
+      const double v = warp_sum(dacc[m]);
+      if (lane == 0) red[warp][m] = v;
+    }
     __syncthreads();
+    if (tid < TGV_DIAG_COUNT) {
+      double v = 0.0;
+      for (int w = 0; w < NT / 32; ++w) v += red[w][tid];
+      const int cta = (blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
+      S.diag_part[(size_t)cta * TGV_DIAG_COUNT + tid] = v;
+    }
   }
 }
 

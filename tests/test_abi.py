@@ -42,7 +42,7 @@ def test_all_named_modes_are_built(mode):
 
 
 def test_invalid_configs_are_rejected_on_host():
-    bad = [tgv.Config(n=4), tgv.Config(n=2048), tgv.Config(n=32, mach=0.0),
+    bad = [tgv.Config(n=4), tgv.Config(n=2048), tgv.Config(n=33), tgv.Config(n=32, mach=0.0),
            tgv.Config(n=32, re=-1.0), tgv.Config(n=32, mu=-1.0), tgv.Config(n=32, tile=9),
            tgv.Config(n=32, zchunk=64)]
     for c in bad:
@@ -91,7 +91,7 @@ def test_sizes_and_stability_limit():
 
 
 def test_tile_shapes_and_workspace():
-    assert tgv.tgv_tile_shapes() == [(32, 8), (16, 16), (16, 8)]
+    assert tgv.tgv_tile_shapes() == [(32, 16), (16, 16), (16, 8)]
     assert tgv.tgv_workspace_bytes(tgv.Config(n=64)) > 0
     assert tgv.tgv_run_host_workspace_bytes(tgv.Config(n=32), 10, 5) >= \
         2 * tgv.tgv_state_bytes(tgv.Config(n=32))
