@@ -183,6 +183,26 @@ int32_t diagnostics_reduce(const tgv_config* cfg, const void* q, double* out_dev
                            void* workspace, size_t ws_bytes, void* stream);
 
 /*
+ * diagnostics_reduce without a workspace argument: the same diagnostics
+ * (same kernels, same result) with the per-block partials kept in a fixed
+ * array inside the library's device memory (1184 * TGV_DIAG_COUNT doubles,
+ * about 95 KB, held on every device that loads the library until the process
+ * exits).  For callers that cannot allocate device memory where they need
+ * the diagnostics (a framework that owns all device allocations, a loop that
+ * must not take cudaMalloc's implicit synchronisation, a plug-in given only
+ * the state).  The paper has no counterpart; this is a library convenience.
+ * q: device, Q layout; out_dev: device, double[TGV_DIAG_COUNT].
+ * The first call on a device looks up the array's address (cudaGetSymbolAddress)
+ * with that device current; make that first call before any stream capture.
+ * All calls share the array: calls whose work overlaps on the GPU (other
+ * streams, other host threads) race and must be serialised by the caller.
+ * Allocates nothing; returns TGV_ERR_ARG if a problem needed more partials
+ * than the array holds (no valid N does).
+ */
+int32_t diagnostics_reduce_noalloc(const tgv_config* cfg, const void* q, double* out_dev,
+                                   void* stream);
+
+/*
  * End-to-end call with HOST buffers: copies q_host_in (Q layout, q_storage,
  * encoded) to the device, advances nsteps RK3 steps with diagnostics every
  * diag_every steps, copies Q^(n+nsteps) to q_host_out and the diagnostics

@@ -179,6 +179,14 @@ def diagnostics_reduce(cfg: Config, q, out, workspace, stream=None) -> None:
                                    _stream(stream)), "diagnostics_reduce")
 
 
+def diagnostics_reduce_noalloc(cfg: Config, q, out, stream=None) -> None:
+    """diagnostics_reduce with the partial sums in the library's own fixed
+    device array instead of a caller workspace (for callers that cannot
+    allocate device memory); calls that overlap on the GPU race."""
+    check(lib().diagnostics_reduce_noalloc(C.byref(cfg.c()), _ptr(q), _ptr(out),
+                                           _stream(stream)), "diagnostics_reduce_noalloc")
+
+
 def tgv_run_host_workspace_bytes(cfg: Config, nsteps: int, diag_every: int) -> int:
     return lib().tgv_run_host_workspace_bytes(C.byref(cfg.c()), int(nsteps), int(diag_every))
 
