@@ -183,6 +183,39 @@ int32_t diagnostics_reduce(const tgv_config* cfg, const void* q, double* out_dev
                            void* workspace, size_t ws_bytes, void* stream);
 
 /*
+ * Discrete adjoint (the paper has none; this is the exact transpose of the
+ * discrete forward operator of rhs_eval / rk_step, evaluated in FP64).
+ * Supported configs: the FP64 mode, and the FP32 mode (FP32 forward states,
+ * FP64 adjoint arithmetic), both with TGV_ENC_PLAIN; others return
+ * TGV_ERR_UNSUPPORTED.  Cotangents (lam, q_bar, grad_mom) are FP64 device
+ * arrays in the Q layout (grad_mom: the 3 momentum fields only).
+ *
+ * tgv_adjoint_workspace_bytes: device scratch for rhs_vjp / rk_step_adjoint.
+ * rhs_vjp: q_bar = (dR/dQ)^T lam at state q (q: device, Q layout, q_storage).
+ * rk_step_adjoint: one RK3 step backwards.  stage_inputs: device, the three
+ *   stage input states Q^n, Q^(n,1), Q^(n,2) of the forward step, stored
+ *   back to back (tgv_state_bytes apart).  q_bar: in, the cotangent of
+ *   Q^(n+1); out, the cotangent of Q^n.  Reverse of Eqs. 3-4 (Sec. 3.1),
+ *   for i = 3, 2, 1:  lam <- A_(i+1) lam + B_i q_bar (A_4 = 0);
+ *   q_bar <- q_bar + dt (dR/dQ(Q^(n,i-1)))^T lam.
+ * tgv_grad_final_ke: J = K(Q_nsteps) (Sec. 4.1, Eq. 11, the grid mean of
+ *   |u|^2/2) and dJ/d(rho u, rho v, rho w) at Q_0 with rho and rho E held
+ *   fixed, by the forward run with a checkpoint every ckpt_every steps, then
+ *   a reverse sweep that recomputes each segment keeping its stage inputs.
+ *   q0: device, Q layout; grad_mom: device double[3 N^3]; j_out: device
+ *   double[1]; workspace: tgv_grad_workspace_bytes(cfg, nsteps, ckpt_every).
+ */
+size_t tgv_adjoint_workspace_bytes(const tgv_config* cfg);
+int32_t rhs_vjp(const tgv_config* cfg, const void* q, const double* lam, double* q_bar,
+                void* workspace, size_t ws_bytes, void* stream);
+int32_t rk_step_adjoint(const tgv_config* cfg, const void* stage_inputs, double* q_bar, double dt,
+                        void* workspace, size_t ws_bytes, void* stream);
+size_t tgv_grad_workspace_bytes(const tgv_config* cfg, int32_t nsteps, int32_t ckpt_every);
+int32_t tgv_grad_final_ke(const tgv_config* cfg, const void* q0, double dt, int32_t nsteps,
+                          int32_t ckpt_every, double* grad_mom, double* j_out, void* workspace,
+                          size_t ws_bytes, void* stream);
+
+/*
  * diagnostics_reduce without a workspace argument: the same diagnostics
  * (same kernels, same result) with the per-block partials kept in a fixed
  * array inside the library's device memory (1184 * TGV_DIAG_COUNT doubles,

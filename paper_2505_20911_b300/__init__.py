@@ -210,3 +210,60 @@ def diagnostics(cfg: Config, q: torch.Tensor, workspace=None) -> dict:
     out = torch.empty(TGV_DIAG_COUNT, dtype=torch.float64, device=q.device)
     diagnostics_reduce(cfg, q, out, ws)
     return dict(zip(DIAG_NAMES, out.cpu().tolist()))
+
+
+# ------------------------------------------------------------------- adjoint
+def tgv_adjoint_workspace_bytes(cfg: Config) -> int:
+    return lib().tgv_adjoint_workspace_bytes(C.byref(cfg.c()))
+
+
+def rhs_vjp(cfg: Config, q, lam, q_bar, workspace=None, stream=None) -> None:
+    """q_bar = (dR/dQ)^T lam at state q (FP64 cotangents)."""
+    ws = workspace if workspace is not None else torch.empty(
+        tgv_adjoint_workspace_bytes(cfg), dtype=torch.uint8, device=q.device)
+    check(lib().rhs_vjp(C.byref(cfg.c()), _ptr(q), _ptr(lam), _ptr(q_bar), _ptr(ws),
+                        ws.numel(), _stream(stream)), "rhs_vjp")
+
+
+def rk_step_adjoint(cfg: Config, stage_inputs, q_bar, dt: float, workspace=None,
+                    stream=None) -> None:
+    """One RK3 step backwards; stage_inputs is a (3, 5, N, N, N) tensor."""
+    ws = workspace if workspace is not None else torch.empty(
+        tgv_adjoint_workspace_bytes(cfg), dtype=torch.uint8, device=q_bar.device)
+    check(lib().rk_step_adjoint(C.byref(cfg.c()), _ptr(stage_inputs), _ptr(q_bar), float(dt),
+                                _ptr(ws), ws.numel(), _stream(stream)), "rk_step_adjoint")
+
+
+def tgv_grad_workspace_bytes(cfg: Config, nsteps: int, ckpt_every: int) -> int:
+    return lib().tgv_grad_workspace_bytes(C.byref(cfg.c()), int(nsteps), int(ckpt_every))
+
+
+def tgv_grad_final_ke(cfg: Config, q0, dt: float, nsteps: int, ckpt_every: int, grad_mom,
+                      j_out, workspace=None, stream=None) -> None:
+    ws = workspace if workspace is not None else torch.empty(
+        tgv_grad_workspace_bytes(cfg, nsteps, ckpt_every), dtype=torch.uint8, device=q0.device)
+    check(lib().tgv_grad_final_ke(C.byref(cfg.c()), _ptr(q0), float(dt), int(nsteps),
+                                  int(ckpt_every), _ptr(grad_mom), _ptr(j_out), _ptr(ws),
+                                  ws.numel(), _stream(stream)), "tgv_grad_final_ke")
+
+
+class TGVFinalKE(torch.autograd.Function):
+    """J = K(Q_nsteps) as a function of the initial momentum (rho u, rho v,
+    rho w) with the initial density and total energy held fixed; backward uses
+    the discrete adjoint (tgv_grad_final_ke), with uniform checkpointing."""
+
+    @staticmethod
+    def forward(ctx, rho_u, rho_v, rho_w, rho, rho_E, cfg: Config, dt: float, nsteps: int,
+                ckpt_every: int):
+        q0 = torch.stack([rho, rho_u, rho_v, rho_w, rho_E]).to(cfg.q_dtype).contiguous()
+        grad = torch.empty((3,) + tuple(rho.shape), dtype=torch.float64, device=q0.device)
+        j = torch.empty(1, dtype=torch.float64, device=q0.device)
+        tgv_grad_final_ke(cfg, q0, dt, nsteps, ckpt_every, grad, j)
+        ctx.save_for_backward(grad)
+        return j[0].clone()
+
+    @staticmethod
+    def backward(ctx, g):
+        (grad,) = ctx.saved_tensors
+        gg = g.to(torch.float64) * grad
+        return gg[0], gg[1], gg[2], None, None, None, None, None, None

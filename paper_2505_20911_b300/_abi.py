@@ -61,6 +61,12 @@ SIGNATURES = {
     "tgv_workspace_bytes": (C.c_size_t, [_CFG]),
     "diagnostics_reduce": (C.c_int32, [_CFG, _P, _P, _P, C.c_size_t, _P]),
     "diagnostics_reduce_noalloc": (C.c_int32, [_CFG, _P, _P, _P]),
+    "tgv_adjoint_workspace_bytes": (C.c_size_t, [_CFG]),
+    "rhs_vjp": (C.c_int32, [_CFG, _P, _P, _P, _P, C.c_size_t, _P]),
+    "rk_step_adjoint": (C.c_int32, [_CFG, _P, _P, C.c_double, _P, C.c_size_t, _P]),
+    "tgv_grad_workspace_bytes": (C.c_size_t, [_CFG, C.c_int32, C.c_int32]),
+    "tgv_grad_final_ke": (C.c_int32, [_CFG, _P, C.c_double, C.c_int32, C.c_int32, _P, _P, _P,
+                                      C.c_size_t, _P]),
     "tgv_run_host_workspace_bytes": (C.c_size_t, [_CFG, C.c_int32, C.c_int32]),
     "tgv_run_host": (C.c_int32, [_CFG, _P, _P, C.c_double, C.c_int32, C.c_int32, _P, _P,
                                  C.c_size_t, _P]),

@@ -95,3 +95,21 @@ def test_tile_shapes_and_workspace():
     assert tgv.tgv_workspace_bytes(tgv.Config(n=64)) > 0
     assert tgv.tgv_run_host_workspace_bytes(tgv.Config(n=32), 10, 5) >= \
         2 * tgv.tgv_state_bytes(tgv.Config(n=32))
+
+
+def test_adjoint_entry_points_validate_on_host():
+    lib = _abi.lib()
+    fake = C.c_void_p(256)
+    c64, c16 = tgv.Config(n=32).c(), tgv.Config(n=32, mode="fp16_fp32").c()
+    assert tgv.tgv_adjoint_workspace_bytes(tgv.Config(n=32)) == 16 * 32 ** 3 * 8
+    assert tgv.tgv_adjoint_workspace_bytes(tgv.Config(n=32, mode="fp16_fp32")) == 0
+    assert lib.rhs_vjp(C.byref(c16), fake, fake, fake, fake, 1 << 30, None) == \
+        _abi.TGV_ERR_UNSUPPORTED
+    assert lib.rhs_vjp(C.byref(c64), fake, fake, fake, None, 0, None) == _abi.TGV_ERR_WORKSPACE
+    assert lib.rk_step_adjoint(C.byref(c64), None, fake, 0.004, fake, 1 << 30, None) == \
+        _abi.TGV_ERR_ARG
+    assert tgv.tgv_grad_workspace_bytes(tgv.Config(n=32), 200, 20) > 10 * 5 * 32 ** 3 * 8
+    assert lib.tgv_grad_final_ke(C.byref(c64), fake, 0.004, 0, 20, fake, fake, fake, 1 << 40,
+                                 None) == _abi.TGV_ERR_ARG
+    assert lib.tgv_grad_final_ke(C.byref(c64), fake, 1.0, 10, 5, fake, fake, fake, 1 << 40,
+                                 None) == _abi.TGV_ERR_UNSTABLE_DT
