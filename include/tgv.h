@@ -216,6 +216,34 @@ int32_t tgv_grad_final_ke(const tgv_config* cfg, const void* q0, double dt, int3
                           size_t ws_bytes, void* stream);
 
 /*
+ * Batched ensemble (a library feature; the paper runs one problem at a
+ * time): `count` independent TGV problems, each with its own N, Re, M and
+ * dt, advanced together by one persistent launch per RK stage over a
+ * flattened list of (instance, tile, z chunk) work items, the launches of
+ * steps_per_graph steps captured in a CUDA graph that tgv_ensemble_run
+ * replays.  Built for the FP32 mode (all four types TGV_F32).
+ * cfgs[i], q_a[i], q_b[i], qt[i], dts[i]: instance i (device buffers of that
+ *   instance's size; q_a holds Q on entry and again after every replay,
+ *   q_b and qt are scratch).  count: 1..64.  steps_per_graph: even, >= 2.
+ * Tile shape and z-chunk length are autotuned at creation by timing
+ *   first-stage launches, which read q_a and write only q_b and qt; if
+ *   cfgs[0].tile / cfgs[0].zchunk are non-zero they are used instead.
+ *   Instance i then matches a single-instance rk_step with tile = the chosen
+ *   tile and zchunk = min(N_i, chosen z-chunk) bit for bit.
+ * The handle (host memory, the graph and its executable) is owned by the
+ * library and released by tgv_ensemble_destroy; no device memory is
+ * allocated.  create synchronises `stream` once.
+ */
+typedef struct tgv_ensemble tgv_ensemble;
+int32_t tgv_ensemble_create(const tgv_config* cfgs, int32_t count, void* const* q_a,
+                            void* const* q_b, void* const* qt, const double* dts,
+                            int32_t steps_per_graph, void* stream, tgv_ensemble** out);
+int32_t tgv_ensemble_run(tgv_ensemble* ens, int32_t replays, void* stream);
+int32_t tgv_ensemble_info(const tgv_ensemble* ens, int32_t* tile, int32_t* zchunk_target,
+                          int32_t* grid, int32_t* items, int32_t* steps_per_graph);
+int32_t tgv_ensemble_destroy(tgv_ensemble* ens);
+
+/*
  * diagnostics_reduce without a workspace argument: the same diagnostics
  * (same kernels, same result) with the per-block partials kept in a fixed
  * array inside the library's device memory (1184 * TGV_DIAG_COUNT doubles,

@@ -267,3 +267,59 @@ class TGVFinalKE(torch.autograd.Function):
         (grad,) = ctx.saved_tensors
         gg = g.to(torch.float64) * grad
         return gg[0], gg[1], gg[2], None, None, None, None, None, None
+
+
+# ------------------------------------------------------------------ ensemble
+class Ensemble:
+    """Owner of a tgv_ensemble handle: `count` FP32 TGV instances of uneven
+    size advanced together (one persistent launch per RK stage, replayed from
+    a CUDA graph of steps_per_graph steps).  Buffers are torch tensors the
+    caller keeps alive; q_a[i] holds instance i's state after every run()."""
+
+    def __init__(self, cfgs, q_a, q_b, qt, dts, steps_per_graph: int = 10, stream=None):
+        n = len(cfgs)
+        arr = (_abi.tgv_config * n)(*[c.c() for c in cfgs])
+        ptrs = lambda ts: (C.c_void_p * n)(*[_ptr(t) for t in ts])
+        self._keep = (list(q_a), list(q_b), list(qt))
+        handle = C.c_void_p()
+        check(lib().tgv_ensemble_create(arr, n, ptrs(q_a), ptrs(q_b), ptrs(qt),
+                                        (C.c_double * n)(*[float(d) for d in dts]),
+                                        int(steps_per_graph), _stream(stream), C.byref(handle)),
+              "tgv_ensemble_create")
+        self.handle = handle
+        self.steps_per_graph = int(steps_per_graph)
+
+    def run(self, replays: int = 1, stream=None) -> None:
+        check(lib().tgv_ensemble_run(self.handle, int(replays), _stream(stream)),
+              "tgv_ensemble_run")
+
+    def info(self) -> dict:
+        vals = [C.c_int32() for _ in range(5)]
+        check(lib().tgv_ensemble_info(self.handle, *[C.byref(v) for v in vals]),
+              "tgv_ensemble_info")
+        keys = ("tile", "zchunk_target", "grid", "items", "steps_per_graph")
+        return dict(zip(keys, (v.value for v in vals)))
+
+    def close(self) -> None:
+        if self.handle:
+            check(lib().tgv_ensemble_destroy(self.handle), "tgv_ensemble_destroy")
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def ensemble_instances(draws=None, device="cuda"):
+    """The 48-instance ensemble workload: (cfgs, dts) from tgv_inputs'
+    seeded draws, dt_i = min(0.004, 0.8 dt_max,i)."""
+    import tgv_inputs
+    draws = draws if draws is not None else tgv_inputs.ensemble_draws()
+    cfgs, dts = [], []
+    for n, re, m in draws:
+        c = Config(n=n, mode="fp32", re=re, mach=m)
+        cfgs.append(c)
+        dts.append(min(0.004, 0.8 * tgv_dt_max(c)))
+    return cfgs, dts

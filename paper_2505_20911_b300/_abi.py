@@ -67,6 +67,13 @@ SIGNATURES = {
     "tgv_grad_workspace_bytes": (C.c_size_t, [_CFG, C.c_int32, C.c_int32]),
     "tgv_grad_final_ke": (C.c_int32, [_CFG, _P, C.c_double, C.c_int32, C.c_int32, _P, _P, _P,
                                       C.c_size_t, _P]),
+    "tgv_ensemble_create": (C.c_int32, [_CFG, C.c_int32, C.POINTER(C.c_void_p),
+                                        C.POINTER(C.c_void_p), C.POINTER(C.c_void_p),
+                                        C.POINTER(C.c_double), C.c_int32, _P,
+                                        C.POINTER(C.c_void_p)]),
+    "tgv_ensemble_run": (C.c_int32, [_P, C.c_int32, _P]),
+    "tgv_ensemble_info": (C.c_int32, [_P] + [C.POINTER(C.c_int32)] * 5),
+    "tgv_ensemble_destroy": (C.c_int32, [_P]),
     "tgv_run_host_workspace_bytes": (C.c_size_t, [_CFG, C.c_int32, C.c_int32]),
     "tgv_run_host": (C.c_int32, [_CFG, _P, _P, C.c_double, C.c_int32, C.c_int32, _P, _P,
                                  C.c_size_t, _P]),

@@ -137,9 +137,11 @@ template <class T> __device__ __forceinline__ T warp_sum(T v) {
   return v;
 }
 
+// The work of one CTA: the TX x TY column tile at (x0, y0), planes z0 to
+// min(z0 + S.zchunk, n); `cta` indexes its diagnostics partials.
 template <class TS, class TT, class TC, class TA, int TX, int TY, int NP, int EPI, bool DIAG>
-__global__ void __launch_bounds__(Geo<TX, TY, NP>::NT, 1)
-stage_kernel(const Problem P, const StageArgs S) {
+__device__ __forceinline__ void stage_tile(const Problem& P, const StageArgs& S, const int x0,
+                                           const int y0, const int z0, const long long cta) {
   using G = Geo<TX, TY, NP>;
   using V = Vec<TC, NP>;
   using IO = UnitIO<TC, NP, TS>;
@@ -154,8 +156,6 @@ stage_kernel(const Problem P, const StageArgs S) {
   const int n = P.n;
   const long long nn = (long long)n * n, n3 = nn * n;
   const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * TXU + tx;
-  const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
-  const int z0 = blockIdx.z * S.zchunk;
   const int z1 = min(z0 + S.zchunk, n);
   const TS* __restrict__ q_in = static_cast<const TS*>(S.q_in);
 
@@ -547,10 +547,17 @@ stage_kernel(const Problem P, const StageArgs S) {
     if (tid < TGV_DIAG_COUNT) {
       double v = 0.0;
       for (int w = 0; w < NT / 32; ++w) v += red[w][tid];
-      const int cta = (blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
       S.diag_part[(size_t)cta * TGV_DIAG_COUNT + tid] = v;
     }
   }
+}
+
+template <class TS, class TT, class TC, class TA, int TX, int TY, int NP, int EPI, bool DIAG>
+__global__ void __launch_bounds__(Geo<TX, TY, NP>::NT, 1)
+stage_kernel(const Problem P, const StageArgs S) {
+  const long long cta = ((long long)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
+  stage_tile<TS, TT, TC, TA, TX, TY, NP, EPI, DIAG>(P, S, blockIdx.x * TX, blockIdx.y * TY,
+                                                    blockIdx.z * S.zchunk, cta);
 }
 
 }  // namespace tgv
