@@ -50,6 +50,10 @@ def parse():
     ap.add_argument("--n", type=int, default=N_DEFAULT)
     ap.add_argument("--no-sweep", action="store_true", help="headline mode only")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-baseline leg")
+    ap.add_argument("--accuracy", action="store_true",
+                    help="precision sweep accuracy report (--n, --accuracy-steps) against "
+                         "the FP64 GPU path; prints one JSON object")
+    ap.add_argument("--accuracy-steps", type=int, default=2000)
     ap.add_argument("--profile-case", default=None, metavar="MODE",
                     help="run 2 warm-up RK3 steps and 1 more step of MODE at --n, then exit "
                          "(the small case an ncu capture of the stage kernel uses)")
@@ -69,6 +73,68 @@ def profile_case(args):
     tgv.rk_step(cfg, qa, qb, qt, dt, 2)
     tgv.rk_step(cfg, qa, qb, qt, dt, 1)
     torch.cuda.synchronize()
+
+
+def accuracy_sweep(args):
+    """Every mode of the sweep at --n for --accuracy-steps steps (dt = 0.00125
+    scaled to the grid), K and enstrophy logged every 10 steps in FP64, against
+    the FP64 GPU path (which the tests pin to the FP64 oracle).  Errors: field
+    relative L2 at the end (rho, momentum vector, rho E), the dissipation rate
+    -dK/dt from central differences of K (max error / max |ref|), the
+    solenoidal dissipation eps^S(t) (max error / max ref) and the mean
+    absolute eps^S difference at every 0.5 time units relative to the mean
+    eps^S there."""
+    import torch
+    import paper_2505_20911_b300 as tgv
+    n, steps = args.n, args.accuracy_steps
+    dt = DT_DEFAULT * 256.0 / n
+    nrec = steps // DIAG_EVERY + 1
+
+    def run(mode, encoding=None):
+        cfg = mode_config(tgv, n, mode)
+        if encoding:
+            cfg = cfg.with_(encoding=encoding)
+        qa = tgv.empty_state(cfg)
+        qb, qt = torch.empty_like(qa), tgv.empty_qt(cfg)
+        tgv.tgv_init(cfg, qa)
+        diag = torch.empty(nrec, tgv.TGV_DIAG_COUNT, dtype=torch.float64, device="cuda")
+        t0 = time.perf_counter()
+        par = tgv.rk_step(cfg, qa, qb, qt, dt, steps, DIAG_EVERY, diag, tgv.empty_workspace(cfg))
+        torch.cuda.synchronize()
+        el = time.perf_counter() - t0
+        q = (qb if par else qa).double()
+        if cfg.encoding == "offset":
+            q[0] += 1.0
+            q[4] += 1.0 / (cfg.gamma * (cfg.gamma - 1.0) * cfg.mach ** 2)
+        d = diag.cpu()
+        del qa, qb, qt
+        torch.cuda.empty_cache()
+        return q, d[:, 0].tolist(), d[:, 3].tolist(), el
+
+    q_ref, K_ref, E_ref, el_ref = run("fp64")
+    diss = lambda K: [-(K[i + 1] - K[i - 1]) / (2 * DIAG_EVERY * dt) for i in range(1, len(K) - 1)]
+    d_ref = diss(K_ref)
+    per = max(1, int(round(0.5 / (DIAG_EVERY * dt))))
+    out = {"n": n, "steps": steps, "dt": dt, "t_end": steps * dt, "reference": "fp64 GPU",
+           "reference_seconds": el_ref, "modes": {}}
+    cases = [(m, None) for m in SWEEP if m != "fp64"] + [("fp16_fp32", "plain")]
+    for mode, enc in cases:
+        q, K, E, el = run(mode, enc)
+        nrm = lambda a: float(torch.linalg.vector_norm(a))
+        rec = {
+            "rho": nrm(q[0] - q_ref[0]) / nrm(q_ref[0]),
+            "momentum": nrm(q[1:4] - q_ref[1:4]) / nrm(q_ref[1:4]),
+            "rhoE": nrm(q[4] - q_ref[4]) / nrm(q_ref[4]),
+            "dKdt": max(abs(a - b) for a, b in zip(diss(K), d_ref)) / max(abs(b) for b in d_ref),
+            "epsS": max(abs(a - b) for a, b in zip(E, E_ref)) / max(abs(b) for b in E_ref),
+            "epsS_mean_abs_at_0.5": (sum(abs(E[i] - E_ref[i]) for i in range(0, nrec, per))
+                                     / sum(abs(E_ref[i]) for i in range(0, nrec, per))),
+            "seconds": el,
+        }
+        out["modes"][mode + ("" if enc is None else f"[{enc}]")] = rec
+        del q
+        torch.cuda.empty_cache()
+    print(json.dumps(out), flush=True)
 
 
 def dist_env():
@@ -384,6 +450,9 @@ def main():
     args = parse()
     if args.profile_case:
         profile_case(args)
+        return
+    if args.accuracy:
+        accuracy_sweep(args)
         return
     rank, world, local = dist_env()
     base = {"metric": METRIC, "unit": UNIT, "n_gpus": world, "steps": args.steps,
