@@ -60,10 +60,8 @@ enum { F_RHO = 0, F_RU, F_RV, F_RW, F_RE, F_U, F_V, F_W, F_P, F_H0, NFLD };
 // Strip fields of the centre plane.
 enum { S_SX = 0, S_SY, S_GX, S_GY, NSTRIP };
 // Ring depth: planes k-2..k+2 are read while the next plane is committed
-// before the first barrier, so the primitives ring needs 6 slots; the s_z
-// ring is written only after that barrier and needs 5.
+// before the first barrier, so the primitives ring needs 6 slots.
 constexpr int NSLOT = 6;
-constexpr int NSZ = 5;
 
 template <int TX, int TY, int NP>
 struct Geo {
@@ -86,8 +84,7 @@ struct Geo {
 template <class TS, class TT, class TC, int TX, int TY, int NP>
 constexpr size_t stage_smem_bytes() {
   using G = Geo<TX, TY, NP>;
-  return sizeof(TC) * ((size_t)NSLOT * NFLD * G::PL + (size_t)NSZ * TX * TY +
-                       (size_t)NSTRIP * G::PL) +
+  return sizeof(TC) * ((size_t)NSLOT * NFLD * G::PL + (size_t)NSTRIP * G::PL) +
          sizeof(TS) * NP * 5 * (size_t)G::PLU + sizeof(TT) * NP * 2 * 5 * (size_t)G::NT;
 }
 // Largest dynamic shared memory a stage CTA may request (B300: 227 KB per CTA,
@@ -150,8 +147,7 @@ __device__ __forceinline__ void stage_tile(const Problem& P, const StageArgs& S,
 
   extern __shared__ __align__(16) unsigned char smem_raw[];
   TC* ring = reinterpret_cast<TC*>(smem_raw);         // [NSLOT][NFLD][PL]
-  TC* szr = ring + NSLOT * NFLD * PL;                  // [NSZ][TX*TY]
-  TC* strips = szr + NSZ * TX * TY;                    // [NSTRIP][PL]
+  TC* strips = ring + NSLOT * NFLD * PL;               // [NSTRIP][PL]
 
   const int n = P.n;
   const long long nn = (long long)n * n, n3 = nn * n;
@@ -305,7 +301,10 @@ __device__ __forceinline__ void stage_tile(const Problem& P, const StageArgs& S,
   const int zbase = z0 - 2;
   const int rxc = 2 + NP * tx, ryc = 2 + ty;
   const int ec = ryc * RX + rxc;        // unit centre in plane layout
-  const int et = ty * TX + NP * tx;     // unit in tile layout (s_z ring)
+  const V zero = V::splat(cvt<TC>(0.0));
+  V szq[5];  // s_z = D_x u + D_y v of the own unit at planes zl-4 .. zl
+#pragma unroll
+  for (int d = 0; d < 5; ++d) szq[d] = zero;
 
   prefetch(zbase);
   cp_async_commit();
@@ -323,31 +322,45 @@ __device__ __forceinline__ void stage_tile(const Problem& P, const StageArgs& S,
     const TC* pk[5];  // ring planes k-2 .. k+2
 #pragma unroll
     for (int d = 0; d < 5; ++d) pk[d] = ring + ((zl - 4 + d - zbase + 2 * NSLOT) % NSLOT) * NFLD * PL;
-    const TC* szk[5];
-#pragma unroll
-    for (int d = 0; d < 5; ++d) szk[d] = szr + ((zl - 4 + d - zbase + 2 * NSZ) % NSZ) * TX * TY;
     TC* st = strips;
 
-    // ---- phase A: s_z taps of plane zl; centre-plane strip fields
+    // ---- phase A: s_z of plane zl (own unit, kept in registers) ...
     {
       const TC* pl = ring + slot * NFLD * PL;
       V cdummy;
       const V dxu = dsum(xt(pl + F_U * PL, ec, cdummy), c_8);
       const V dyv = dsum(yt(pl + F_V * PL, ec), c_8);
-      (c_inv12h * (dxu + dyv)).store(szr + ((zl - zbase) % NSZ) * TX * TY + et);
+#pragma unroll
+      for (int d = 0; d < 4; ++d) szq[d] = szq[d + 1];
+      szq[4] = c_inv12h * (dxu + dyv);
     }
-    V div = V::splat(cvt<TC>(0.0));
+    // ... then, for centre plane k: the strip fields of the tile and its halo,
+    // and every z-direction term of the own unit (its z taps of u, v, w are
+    // shared with the strips).  The partial sums stay in registers across the
+    // barrier and phase B adds the x and y directions.
+    V fc[5], uc[3], h0c = zero, div = zero;
+    V suf[5], udf[5], d2u[3], ds[3];
+    V d2h = zero, dus = zero;
+    V grad[3][3];  // grad[i][j] = raw D_j u_i (diagnostics)
+#pragma unroll
+    for (int c = 0; c < 5; ++c) { suf[c] = zero; udf[c] = zero; fc[c] = zero; }
+#pragma unroll
+    for (int i = 0; i < 3; ++i) { d2u[i] = zero; ds[i] = zero; uc[i] = zero; }
     if (k >= z0) {
       const TC* P0 = pk[2];
       auto ztw = [&](int fld, int e) -> Taps<V> {
         return {V::load(pk[0] + fld * PL + e), V::load(pk[1] + fld * PL + e),
                 V::load(pk[3] + fld * PL + e), V::load(pk[4] + fld * PL + e)};
       };
-      // own unit (tile point): everything
+      // own unit (tile point)
       {
-        V uc;
-        const Taps<V> ux = xt(P0 + F_U * PL, ec, uc);
+#pragma unroll
+        for (int c = 0; c < 5; ++c) fc[c] = V::load(P0 + c * PL + ec);
+        h0c = V::load(P0 + F_H0 * PL + ec);
+        const Taps<V> ux = xt(P0 + F_U * PL, ec, uc[0]);
         const Taps<V> uy = yt(P0 + F_U * PL, ec), vy = yt(P0 + F_V * PL, ec);
+        uc[1] = V::load(P0 + F_V * PL + ec);
+        uc[2] = V::load(P0 + F_W * PL + ec);
         const Taps<V> uz = ztw(F_U, ec), vz = ztw(F_V, ec), wz = ztw(F_W, ec);
         const V dxu = c_inv12h * dsum(ux, c_8);
         const V dyv = c_inv12h * dsum(vy, c_8);
@@ -360,6 +373,41 @@ __device__ __forceinline__ void stage_tile(const Problem& P, const StageArgs& S,
         const V ezvw = dsum(tmul(vz, wz), c_8);
         (c_2 * c_inv12h * (eyuv + ezuw)).store(st + S_GX * PL + ec);
         (c_2 * c_inv12h * ezvw).store(st + S_GY * PL + ec);
+
+        // z-direction terms (j = 2)
+        const Taps<V>& U = wz;
+        const Taps<V> aU = tscale(c_alpha, U);
+        const Taps<V> Pt = ztw(F_P, ec);
+#pragma unroll
+        for (int c = 0; c < 5; ++c) {
+          const Taps<V> F = ztw(c, ec);
+          const V dF = dsum(F, c_8);
+          udf[c] = fma(uc[2], dF, udf[c]);
+          if (c == 0) continue;
+          Taps<V> g;
+          if (c == 3) g = tfma(aU, F, Pt);                      // a w rho w + p
+          else if (c == 4) g = tmul(U, taxpy(c_alpha, F, Pt));  // w (a rho E + p)
+          else g = tmul(aU, F);
+          suf[c] = suf[c] + dsum(g, c_8);
+          if (c == 3) suf[0] = fma(c_alpha, dF, suf[0]);  // D_z(rho w)
+        }
+        const Taps<V>* UZ[3] = {&uz, &vz, &wz};
+#pragma unroll
+        for (int i = 0; i < 3; ++i) {
+          const V w8 = (i == 2) ? c_43 : c_one;
+          d2u[i] = fma(w8, d2sum(*UZ[i], uc[i], c_16, c_m30), d2u[i]);
+          if constexpr (DIAG) grad[i][2] = dsum(*UZ[i], c_8);
+        }
+        {
+          const Taps<V> H = tfma(tscale(c_nu6, U), U, ztw(F_H0, ec));
+          const V Hc = fma(c_nu6 * uc[2], uc[2], h0c);
+          d2h = d2h + d2sum(H, Hc, c_16, c_m30);
+        }
+        {
+          const Taps<V> Sj = {szq[0], szq[1], szq[3], szq[4]};
+          ds[2] = dsum(Sj, c_8);
+          dus = dus + dsum(tmul(U, Sj), c_8);
+        }
       }
       // halo strips: x-halo units need s_x and G_x, y-halo units s_y and G_y
 #pragma unroll
@@ -393,31 +441,14 @@ __device__ __forceinline__ void stage_tile(const Problem& P, const StageArgs& S,
     }
     __syncthreads();
 
-    // ---- phase B: all terms at plane k for this thread's unit
+    // ---- phase B: x- and y-direction terms of the own unit, assembly, epilogue
     if (k >= z0 && active_xy) {
       const TC* P0 = pk[2];
-      V fc[5];
 #pragma unroll
-      for (int c = 0; c < 5; ++c) fc[c] = V::load(P0 + c * PL + ec);
-      const V uc[3] = {V::load(P0 + F_U * PL + ec), V::load(P0 + F_V * PL + ec),
-                       V::load(P0 + F_W * PL + ec)};
-      const V h0c = V::load(P0 + F_H0 * PL + ec);
-      const V zero = V::splat(cvt<TC>(0.0));
-      V suf[5], udf[5], d2u[3], ds[3];
-#pragma unroll
-      for (int c = 0; c < 5; ++c) { suf[c] = zero; udf[c] = zero; }
-#pragma unroll
-      for (int i = 0; i < 3; ++i) { d2u[i] = zero; ds[i] = zero; }
-      V d2h = zero, dus = zero;
-      V grad[3][3];  // grad[i][j] = raw D_j u_i (diagnostics)
-
-#pragma unroll
-      for (int j = 0; j < 3; ++j) {
+      for (int j = 0; j < 2; ++j) {
         auto tap = [&](int fld) -> Taps<V> {
           if (j == 0) { V cd; return xt(P0 + fld * PL, ec, cd); }
-          if (j == 1) return yt(P0 + fld * PL, ec);
-          return {V::load(pk[0] + fld * PL + ec), V::load(pk[1] + fld * PL + ec),
-                  V::load(pk[3] + fld * PL + ec), V::load(pk[4] + fld * PL + ec)};
+          return yt(P0 + fld * PL, ec);
         };
         const Taps<V> U = tap(F_U + j);
         const Taps<V> aU = tscale(c_alpha, U);
@@ -454,8 +485,7 @@ __device__ __forceinline__ void stage_tile(const Problem& P, const StageArgs& S,
         {
           Taps<V> Sj;
           if (j == 0) { V cd; Sj = xt(st + S_SX * PL, ec, cd); }
-          else if (j == 1) Sj = yt(st + S_SY * PL, ec);
-          else Sj = {V::load(szk[0] + et), V::load(szk[1] + et), V::load(szk[3] + et), V::load(szk[4] + et)};
+          else Sj = yt(st + S_SY * PL, ec);
           ds[j] = dsum(Sj, c_8);
           dus = dus + dsum(tmul(U, Sj), c_8);
         }
