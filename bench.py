@@ -246,6 +246,22 @@ def profile_traffic(mode, n):
         return None
 
 
+def reduce_max(v: float, dist, device) -> float:
+    """Max of a per-rank scalar over all ranks (the timing rule: the slowest
+    rank's time); identity without a process group."""
+    if dist is None:
+        return v
+    import torch
+    t = torch.tensor([v], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_value(points_per_rank: int, steps: int, world: int, max_ms: float) -> float:
+    """Weak-scaling aggregate: all ranks' point-steps over the slowest rank's time."""
+    return world * points_per_rank * steps / (max_ms * 1e-3)
+
+
 def run_ours(args, rank, world, local):
     import torch
     import paper_2505_20911_b300 as tgv
@@ -263,11 +279,7 @@ def run_ours(args, rank, world, local):
         torch.cuda.synchronize()
 
     def max_over_ranks(v):
-        if dist is None:
-            return v
-        t = torch.tensor([v], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
+        return reduce_max(v, dist, dev)
 
     n, dt, K, W = args.n, DT_DEFAULT * (256.0 / args.n), args.steps, max(args.warmup, 3)
     stream = torch.cuda.current_stream()
@@ -302,9 +314,12 @@ def run_ours(args, rank, world, local):
         ms, par, diag, nrec = timed_steps(cfg, qa, qb, qt, ws, K, DIAG_EVERY)
     ms = max_over_ranks(ms)
     ms_step = ms / K
-    value = world * n ** 3 * K / (ms * 1e-3)
+    value = whole_job_value(n ** 3, K, world, ms)
     diag_last = diag[nrec - 1].cpu().tolist()
-    launches = 3 * K + 2 * nrec
+    # 3 stage launches per step (the first of each logged step fuses the
+    # diagnostics), one final-reduction launch per logged step, and the
+    # standalone two-pass reduction of the last state when K % 10 == 0
+    launches = 3 * K + (K + DIAG_EVERY - 1) // DIAG_EVERY + (2 if K % DIAG_EVERY == 0 else 0)
 
     # ---- roofline of the dominant kernel (the fused stage), on the same stream
     reps = max(10, min(K, 60))
@@ -367,7 +382,7 @@ def run_ours(args, rank, world, local):
 
     # ---- the rest of the precision sweep, each next to FP64
     modes = {}
-    if not args.no_sweep:
+    if not args.no_sweep and world == 1:
         for mode in SWEEP:
             c, a, b, t, w = setup(mode)
             steps = 4 if c.compute_dtype == torch.float64 and mode != "spdp" else 20
@@ -385,13 +400,96 @@ def run_ours(args, rank, world, local):
         for mode in modes:
             modes[mode]["vs_fp64"] = modes[mode]["value"] / modes["fp64"]["value"]
 
+    extra = {} if (args.no_sweep or world > 1) else extra_workloads(args, tgv, torch, dev, stream,
+                                                                   peaks)
+
     if dist is not None:
         dist.destroy_process_group()
     return {
         "value": value, "ms_per_step": ms_step, "roofline": roofline, "e2e": e2e,
         "gpu_launches": launches, "clocks": clk.summary(), "modes": modes,
-        "diag_last": dict(zip(tgv.DIAG_NAMES, diag_last)), "dt": dt,
+        "diag_last": dict(zip(tgv.DIAG_NAMES, diag_last)), "dt": dt, **extra,
     }
+
+
+def extra_workloads(args, tgv, torch, dev, stream, peaks):
+    """The other configurations' throughput (each timed with CUDA events):
+    512^3 half-single vs single (dt = 0.000625), the 64^3 adjoint (FP64 and
+    FP32-forward / FP64-adjoint, 200 steps, checkpoint every 20) and the
+    48-instance ensemble (FP32, 500 steps) against the sum of solo runs."""
+    out = {}
+
+    def ev_time(fn):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1)
+
+    # 512^3 (config: FP16 storage / FP32 compute against FP32 / FP32)
+    big = {}
+    for mode in ("fp16_fp32", "fp32"):
+        cfg = mode_config(tgv, 512, mode)
+        qa = tgv.empty_state(cfg, dev)
+        qb, qt = torch.empty_like(qa), tgv.empty_qt(cfg, dev)
+        tgv.tgv_init(cfg, qa)
+        tgv.rk_step(cfg, qa, qb, qt, 0.000625, 3, 0, None, None, stream)
+        steps = 10
+        ms = ev_time(lambda: tgv.rk_step(cfg, qa, qb, qt, 0.000625, steps, 0, None, None, stream))
+        v = 512 ** 3 * steps / (ms * 1e-3)
+        bpp = alg_bytes_per_point_step(cfg, torch)
+        big[mode] = {"value": v, "ms_per_step": ms / steps, "alg_GBs": bpp * v / 1e9,
+                     "hbm_frac": bpp * v / 1e9 / peaks["hbm_gbs"]}
+        del qa, qb, qt
+        torch.cuda.empty_cache()
+    big["fp16_vs_fp32"] = big["fp16_fp32"]["value"] / big["fp32"]["value"]
+    out["n512"] = big
+
+    # adjoint: 64^3, 200 steps, checkpoint every 20
+    adj = {}
+    for mode in ("fp64", "fp32"):
+        cfg = tgv.Config(n=64, mode=mode)
+        q0 = tgv.empty_state(cfg, dev)
+        tgv.tgv_init(cfg, q0)
+        g = torch.empty((3, 64, 64, 64), dtype=torch.float64, device=dev)
+        j = torch.empty(1, dtype=torch.float64, device=dev)
+        ws = torch.empty(tgv.tgv_grad_workspace_bytes(cfg, 200, 20), dtype=torch.uint8, device=dev)
+        tgv.tgv_grad_final_ke(cfg, q0, 0.004, 200, 20, g, j, ws, stream)
+        ms = ev_time(lambda: tgv.tgv_grad_final_ke(cfg, q0, 0.004, 200, 20, g, j, ws, stream))
+        qa, qb, qt = q0.clone(), torch.empty_like(q0), tgv.empty_qt(cfg, dev)
+        fwd = ev_time(lambda: tgv.rk_step(cfg, qa, qb, qt, 0.004, 200, 0, None, None, stream))
+        adj["fp64" if mode == "fp64" else "fp32_fwd_fp64_adj"] = {
+            "grad_ms": ms, "forward_ms": fwd, "grad_over_forward": ms / fwd, "J": float(j[0])}
+        del q0, g, ws, qa, qb, qt
+        torch.cuda.empty_cache()
+    out["adjoint_64"] = adj
+
+    # ensemble: 48 instances, FP32, 500 steps, one graph of 10 steps replayed
+    cfgs, dts = tgv.ensemble_instances()
+    bufs = []
+    for c in cfgs:
+        q = tgv.empty_state(c, dev)
+        tgv.tgv_init(c, q)
+        bufs.append((q, torch.empty_like(q), tgv.empty_qt(c, dev)))
+    ens = tgv.Ensemble(cfgs, [b[0] for b in bufs], [b[1] for b in bufs], [b[2] for b in bufs],
+                       dts, steps_per_graph=10, stream=stream)
+    info = ens.info()
+    ens.run(1, stream)
+    ms = ev_time(lambda: ens.run(50, stream))
+    pts = sum(c.n ** 3 for c in cfgs)
+    solo = 0.0
+    for c, d, b in zip(cfgs, dts, bufs):
+        cc = c.with_(tile=info["tile"], zchunk=min(c.n, info["zchunk_target"]))
+        solo += ev_time(lambda: tgv.rk_step(cc, b[0], b[1], b[2], d, 500, 0, None, None, stream))
+    ens.close()
+    out["ensemble_48"] = {"value": pts * 500 / (ms * 1e-3), "unit": UNIT, "ms": ms,
+                          "points": pts, "steps": 500, "solo_sum_ms": solo,
+                          "speedup_vs_solo_sum": solo / ms, **info}
+    del bufs
+    torch.cuda.empty_cache()
+    return out
 
 
 # ------------------------------------------------------------ CPU oracle legs
@@ -409,11 +507,19 @@ def oracle_sample(n_sample, steps=1):
 
 
 def cpu_baseline(n):
+    """One RK substep (a third of a step) of the oracle on the full grid."""
     import torch
-    v, el = oracle_sample(n, 1)
-    return {"value": v, "unit": UNIT, "cores": torch.get_num_threads(), "kind": "oracle",
-            "sample": f"1 RK3 step of the FP64 oracle on the full {n}^3 TGV grid "
-                      f"({el:.1f} s on the host cores)"}
+    import oracle
+    flow = oracle.Flow(n=n)
+    q = oracle.initial_condition(flow)
+    qt = torch.zeros_like(q)
+    t0 = time.perf_counter()
+    oracle.rk_substep(flow, q, qt, 0, DT_DEFAULT * 256.0 / n)
+    el = time.perf_counter() - t0
+    return {"value": n ** 3 / (3.0 * el), "unit": UNIT, "cores": torch.get_num_threads(),
+            "kind": "oracle",
+            "sample": f"1 RK substep (1/3 step) of the FP64 oracle on the full {n}^3 TGV grid, "
+                      f"{el:.1f} s on the host cores, scaled to point-steps/s"}
 
 
 def run_reference(args, rank, world):
@@ -483,6 +589,9 @@ def main():
                 config=config, roofline=res["roofline"], e2e=res["e2e"],
                 gpu_launches=res["gpu_launches"], clocks=res["clocks"], modes=res["modes"],
                 diag_last=res["diag_last"])
+    for key in ("n512", "adjoint_64", "ensemble_48"):
+        if key in res:
+            line[key] = res[key]
     if world == 1 and not args.no_cpu:
         line["cpu_baseline"] = cpu_baseline(args.n)
     print(json.dumps(line), flush=True)

@@ -267,7 +267,7 @@ int32_t rhs_eval(const tgv_config* cfg, const void* q, void* r, void* stream) {
 
 static int32_t substep_impl(const tgv_config* cfg, const void* q_in, void* q_out, void* qt,
                             int32_t i, double dt, double* diag_part, long long* ctas,
-                            void* stream) {
+                            void* stream, bool write_qt = true) {
   StageArgs S;
   std::memset(&S, 0, sizeof(S));
   S.q_in = q_in;
@@ -278,7 +278,7 @@ static int32_t substep_impl(const tgv_config* cfg, const void* q_in, void* q_out
   S.b = RK_B[i];
   S.dt = dt;
   S.read_qt = (i != 0);
-  S.write_qt = 1;
+  S.write_qt = write_qt ? 1 : 0;
   return launch_stage_common(cfg, S, false, (cudaStream_t)stream, ctas);
 }
 
@@ -332,7 +332,8 @@ int32_t rk_step(const tgv_config* cfg, void* q_a, void* q_b, void* qt, double dt
       // the first substep of a logged step also reduces the diagnostics of Q^m
       long long ctas = 0;
       double* part = (log && i == 0) ? static_cast<double*>(workspace) : nullptr;
-      s = substep_impl(cfg, buf[cur], buf[cur ^ 1], qt, i, dt, part, &ctas, stream);
+      // the last substep's Qt is never read (A_1 = 0 restarts it): not stored
+      s = substep_impl(cfg, buf[cur], buf[cur ^ 1], qt, i, dt, part, &ctas, stream, i != 2);
       if (s != TGV_OK) return s;
       if (part) {
         diag_final_kernel<<<1, 32 * TGV_DIAG_COUNT, 0, (cudaStream_t)stream>>>(

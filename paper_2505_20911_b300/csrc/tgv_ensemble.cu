@@ -40,7 +40,7 @@ struct EnsTable {
 template <int TX, int TY>
 __global__ void __launch_bounds__(Geo<TX, TY, 2>::NT, 1)
 ensemble_stage_kernel(const EnsTable T, const double a, const double b, const int read_qt,
-                      const int parity) {
+                      const int write_qt, const int parity) {
   for (int item = blockIdx.x; item < T.total_items; item += gridDim.x) {
     int ii = 0;
     while (ii + 1 < T.count && T.inst[ii + 1].item_off <= item) ++ii;
@@ -60,7 +60,7 @@ ensemble_stage_kernel(const EnsTable T, const double a, const double b, const in
     S.b = b;
     S.dt = I.dt;
     S.read_qt = read_qt;
-    S.write_qt = 1;
+    S.write_qt = write_qt;
     S.zchunk = I.zchunk;
     stage_tile<float, float, float, float, TX, TY, 2, EPI_RK, false>(I.P, S, bx * TX, by * TY,
                                                                       bz * I.zchunk, 0);
@@ -69,16 +69,16 @@ ensemble_stage_kernel(const EnsTable T, const double a, const double b, const in
 }
 
 using EnsFn = cudaError_t (*)(const EnsTable&, int grid, double a, double b, int read_qt,
-                              int parity, cudaStream_t);
+                              int write_qt, int parity, cudaStream_t);
 
 template <int TX, int TY>
 static cudaError_t ens_launch(const EnsTable& T, int grid, double a, double b, int read_qt,
-                              int parity, cudaStream_t st) {
+                              int write_qt, int parity, cudaStream_t st) {
   auto kern = ensemble_stage_kernel<TX, TY>;
   const size_t smem = stage_smem_bytes<float, float, float, TX, TY, 2>();
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  kern<<<grid, dim3(TX / 2, TY), smem, st>>>(T, a, b, read_qt, parity);
+  kern<<<grid, dim3(TX / 2, TY), smem, st>>>(T, a, b, read_qt, write_qt, parity);
   return cudaGetLastError();
 }
 
@@ -170,10 +170,10 @@ static int32_t ens_check(const tgv_config* cfgs, int32_t count, void* const* q_a
 // Time `reps` first-stage launches of a candidate (reads Q_a only).
 static float ens_time(const EnsTable& T, int tile, int grid, int reps, cudaStream_t st,
                       cudaEvent_t e0, cudaEvent_t e1) {
-  if (ENS_FN[tile](T, grid, RK_A[0], RK_B[0], 0, 0, st) != cudaSuccess) return -1.f;
+  if (ENS_FN[tile](T, grid, RK_A[0], RK_B[0], 0, 1, 0, st) != cudaSuccess) return -1.f;
   cudaEventRecord(e0, st);
   for (int r = 0; r < reps; ++r)
-    if (ENS_FN[tile](T, grid, RK_A[0], RK_B[0], 0, 0, st) != cudaSuccess) return -1.f;
+    if (ENS_FN[tile](T, grid, RK_A[0], RK_B[0], 0, 1, 0, st) != cudaSuccess) return -1.f;
   cudaEventRecord(e1, st);
   if (cudaEventSynchronize(e1) != cudaSuccess) return -1.f;
   float ms = 0.f;
@@ -256,8 +256,8 @@ int32_t tgv_ensemble_create(const tgv_config* cfgs, int32_t count, void* const* 
   bool ok = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
   for (int m = 0; ok && m < steps_per_graph; ++m)
     for (int i = 0; ok && i < 3; ++i)
-      ok = ENS_FN[E->tile](E->table, E->grid, RK_A[i], RK_B[i], i != 0, (3 * m + i) & 1, cap) ==
-           cudaSuccess;
+      ok = ENS_FN[E->tile](E->table, E->grid, RK_A[i], RK_B[i], i != 0, i != 2, (3 * m + i) & 1,
+                           cap) == cudaSuccess;
   cudaGraph_t g = nullptr;
   const bool ended = cudaStreamEndCapture(cap, &g) == cudaSuccess;
   ok = ok && ended && g;
