@@ -1,8 +1,8 @@
 // tgv_vec.cuh - a "unit" of NP consecutive x points handled by one thread.
 //
 // Vec<T, 1> is a scalar; Vec<float, 2> packs two FP32 lanes and uses the
-// sm_100+ paired FP32 instructions (add/sub/mul/fma .f32x2), which issue once
-// for both lanes; Vec<__half, 2> is __half2.  All stencil arithmetic of the
+// sm_100+ paired FP32 intrinsics (__fadd2_rn, __fmul2_rn, __ffma2_rn), which
+// issue once for both lanes; Vec<__half, 2> is __half2.  All stencil arithmetic of the
 // stage kernel is written once against this interface.
 #pragma once
 
@@ -38,13 +38,6 @@ __device__ __forceinline__ Vec<double, 1> rcp(Vec<double, 1> a) { return Vec<dou
 __device__ __forceinline__ Vec<float, 1> rcp(Vec<float, 1> a) { return Vec<float, 1>(__frcp_rn(a.v)); }
 
 // ------------------------------------------------------ two FP32 lanes (f32x2)
-__device__ __forceinline__ unsigned long long f2_bits(float2 a) {
-  return (unsigned long long)__float_as_uint(a.x) | ((unsigned long long)__float_as_uint(a.y) << 32);
-}
-__device__ __forceinline__ float2 f2_from(unsigned long long b) {
-  return make_float2(__uint_as_float((unsigned)b), __uint_as_float((unsigned)(b >> 32)));
-}
-
 template <> struct Vec<float, 2> {
   float2 v;
   __device__ __forceinline__ Vec() {}
@@ -59,27 +52,17 @@ template <> struct Vec<float, 2> {
   static __device__ __forceinline__ Vec mix(const Vec& a, const Vec& b) { return Vec(a.v.y, b.v.x); }
 };
 __device__ __forceinline__ Vec<float, 2> operator+(Vec<float, 2> a, Vec<float, 2> b) {
-  unsigned long long d;
-  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(f2_bits(a.v)), "l"(f2_bits(b.v)));
-  return Vec<float, 2>(f2_from(d));
-}
-__device__ __forceinline__ Vec<float, 2> operator-(Vec<float, 2> a, Vec<float, 2> b) {
-  unsigned long long d;
-  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(f2_bits(a.v)), "l"(f2_bits(b.v)));
-  return Vec<float, 2>(f2_from(d));
-}
-__device__ __forceinline__ Vec<float, 2> operator*(Vec<float, 2> a, Vec<float, 2> b) {
-  unsigned long long d;
-  asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(f2_bits(a.v)), "l"(f2_bits(b.v)));
-  return Vec<float, 2>(f2_from(d));
+  return Vec<float, 2>(__fadd2_rn(a.v, b.v));
 }
 __device__ __forceinline__ Vec<float, 2> operator-(Vec<float, 2> a) { return Vec<float, 2>(-a.v.x, -a.v.y); }
+__device__ __forceinline__ Vec<float, 2> operator-(Vec<float, 2> a, Vec<float, 2> b) {
+  return Vec<float, 2>(__fadd2_rn(a.v, make_float2(-b.v.x, -b.v.y)));
+}
+__device__ __forceinline__ Vec<float, 2> operator*(Vec<float, 2> a, Vec<float, 2> b) {
+  return Vec<float, 2>(__fmul2_rn(a.v, b.v));
+}
 __device__ __forceinline__ Vec<float, 2> fma(Vec<float, 2> a, Vec<float, 2> b, Vec<float, 2> c) {
-  unsigned long long d;
-  asm("fma.rn.f32x2 %0, %1, %2, %3;"
-      : "=l"(d)
-      : "l"(f2_bits(a.v)), "l"(f2_bits(b.v)), "l"(f2_bits(c.v)));
-  return Vec<float, 2>(f2_from(d));
+  return Vec<float, 2>(__ffma2_rn(a.v, b.v, c.v));
 }
 __device__ __forceinline__ Vec<float, 2> rcp(Vec<float, 2> a) {
   return Vec<float, 2>(__frcp_rn(a.v.x), __frcp_rn(a.v.y));
