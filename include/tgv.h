@@ -59,6 +59,10 @@ typedef enum { TGV_ENC_PLAIN = 0, TGV_ENC_OFFSET = 1 } tgv_encoding;
 
 /* Flags of tgv_config.flags */
 #define TGV_FLAG_ALLOW_UNSTABLE_DT 1  /* skip the dt stability check            */
+#define TGV_FLAG_CHECK_FINITE 2       /* rk_step: after each diagnostics record,
+                                         synchronise the stream and stop with
+                                         TGV_ERR_NONFINITE if the state holds a
+                                         NaN or Inf (costs one sync per record) */
 
 /*
  * One TGV problem.  Physics follows Sec. 3.1 / Sec. 4.1 (nondimensional):
@@ -152,7 +156,10 @@ int32_t rhs_eval(const tgv_config* cfg, const void* q, void* r, void* stream);
  * workspace: device scratch of tgv_workspace_bytes(cfg) bytes (nullable
  *   when diag_every = 0).
  * Returns TGV_ERR_UNSTABLE_DT if dt > tgv_dt_max(cfg) and the flag
- * TGV_FLAG_ALLOW_UNSTABLE_DT is not set.
+ * TGV_FLAG_ALLOW_UNSTABLE_DT is not set.  With TGV_FLAG_CHECK_FINITE (and
+ * diag_every > 0) it stops at the first record whose non-finite count is not
+ * zero and returns TGV_ERR_NONFINITE; *parity_out then names the buffer
+ * holding that recorded state, and the records up to it are valid.
  */
 int32_t rk_step(const tgv_config* cfg, void* q_a, void* q_b, void* qt, double dt,
                 int32_t nsteps, int32_t diag_every, double* diag_dev,

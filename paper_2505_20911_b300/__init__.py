@@ -55,6 +55,7 @@ class Config:
     tile: int = 0
     zchunk: int = 0
     allow_unstable_dt: bool = False
+    check_finite: bool = False
     length: float = 2.0 * math.pi
 
     def with_(self, **kw) -> "Config":
@@ -80,7 +81,8 @@ class Config:
             q_storage=qs, qt_storage=qts, compute=comp, accumulate=acc,
             encoding={"plain": TGV_ENC_PLAIN, "offset": TGV_ENC_OFFSET}[self.encoding],
             tile=self.tile, zchunk=self.zchunk,
-            flags=TGV_FLAG_ALLOW_UNSTABLE_DT if self.allow_unstable_dt else 0,
+            flags=(TGV_FLAG_ALLOW_UNSTABLE_DT if self.allow_unstable_dt else 0)
+            | (_abi.TGV_FLAG_CHECK_FINITE if self.check_finite else 0),
             length=self.length, gamma=self.gamma, mach=self.mach, re=self.re, pr=self.pr,
             mu=self.mu)
 

@@ -19,6 +19,7 @@ TGV_ERR_NONFINITE, TGV_ERR_UNSTABLE_DT, TGV_ERR_TIMEOUT, TGV_ERR_WORKSPACE = -4,
 TGV_SPLIT_BLAISDELL, TGV_SPLIT_DIVERGENCE = 0, 1
 TGV_ENC_PLAIN, TGV_ENC_OFFSET = 0, 1
 TGV_FLAG_ALLOW_UNSTABLE_DT = 1
+TGV_FLAG_CHECK_FINITE = 2
 TGV_DIAG_COUNT = 10
 TGV_ABI_VERSION = 1
 

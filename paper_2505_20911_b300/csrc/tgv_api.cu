@@ -336,18 +336,39 @@ int32_t rk_step(const tgv_config* cfg, void* q_a, void* q_b, void* qt, double dt
       s = substep_impl(cfg, buf[cur], buf[cur ^ 1], qt, i, dt, part, &ctas, stream, i != 2);
       if (s != TGV_OK) return s;
       if (part) {
-        diag_final_kernel<<<1, 32 * TGV_DIAG_COUNT, 0, (cudaStream_t)stream>>>(
-            P, part, (int)ctas, diag_dev + (size_t)rec * TGV_DIAG_COUNT);
+        double* record = diag_dev + (size_t)rec * TGV_DIAG_COUNT;
+        diag_final_kernel<<<1, 32 * TGV_DIAG_COUNT, 0, (cudaStream_t)stream>>>(P, part, (int)ctas,
+                                                                              record);
         TGV_CUDA_TRY(cudaGetLastError());
         ++rec;
+        if (cfg->flags & TGV_FLAG_CHECK_FINITE) {
+          double bad = 0.0;
+          TGV_CUDA_TRY(cudaMemcpyAsync(&bad, record + 9, sizeof(double), cudaMemcpyDeviceToHost,
+                                       (cudaStream_t)stream));
+          TGV_CUDA_TRY(cudaStreamSynchronize((cudaStream_t)stream));
+          if (bad != 0.0) {  // the recorded state is the stage-1 input, buf[cur]
+            if (parity_out) *parity_out = cur;
+            return TGV_ERR_NONFINITE;
+          }
+        }
       }
       cur ^= 1;
     }
   }
   if (diag_every > 0 && nsteps % diag_every == 0) {
-    s = diagnostics_reduce(cfg, buf[cur], diag_dev + (size_t)rec * TGV_DIAG_COUNT, workspace,
-                           ws_bytes, stream);
+    double* record = diag_dev + (size_t)rec * TGV_DIAG_COUNT;
+    s = diagnostics_reduce(cfg, buf[cur], record, workspace, ws_bytes, stream);
     if (s != TGV_OK) return s;
+    if (cfg->flags & TGV_FLAG_CHECK_FINITE) {
+      double bad = 0.0;
+      TGV_CUDA_TRY(cudaMemcpyAsync(&bad, record + 9, sizeof(double), cudaMemcpyDeviceToHost,
+                                   (cudaStream_t)stream));
+      TGV_CUDA_TRY(cudaStreamSynchronize((cudaStream_t)stream));
+      if (bad != 0.0) {
+        if (parity_out) *parity_out = cur;
+        return TGV_ERR_NONFINITE;
+      }
+    }
   }
   if (parity_out) *parity_out = cur;
   return TGV_OK;
