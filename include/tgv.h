@@ -54,7 +54,11 @@ typedef enum {
   TGV_ERR_WORKSPACE = -7     /* workspace null or smaller than required        */
 } tgv_status;
 
-typedef enum { TGV_SPLIT_BLAISDELL = 0, TGV_SPLIT_DIVERGENCE = 1 } tgv_split;
+/* Convective split forms (Sec. 2.3.1, Eq. 1; the study of Sec. 4.2):
+ * Blaisdell quadratic (default), plain divergence form, KGP cubic.  KGP is
+ * built for the FP64, FP32 and Q FP32 / Qt FP16 modes of rk_step/rhs_eval
+ * (TGV_ERR_UNSUPPORTED elsewhere, in the adjoint and in the ensemble). */
+typedef enum { TGV_SPLIT_BLAISDELL = 0, TGV_SPLIT_DIVERGENCE = 1, TGV_SPLIT_KGP = 2 } tgv_split;
 typedef enum { TGV_ENC_PLAIN = 0, TGV_ENC_OFFSET = 1 } tgv_encoding;
 
 /* Flags of tgv_config.flags */

@@ -33,7 +33,12 @@ used):
       heat flux q_j = -kappa dT/dx_j, kappa = mu / ((gamma-1) M^2 Pr Re).
   R3  Blaisdell split: C_phi = 1/2 sum_j [ D_j(rho u_j phi) + u_j D_j(rho phi)
       + rho phi D_j u_j ]; pressure terms in divergence form.  The plain
-      divergence form C_phi = sum_j D_j(rho u_j phi) is kept as a foil.
+      divergence form C_phi = sum_j D_j(rho u_j phi) is kept as a foil, and
+      the cubic Kennedy-Gruber-Pirozzoli split of the robustness study
+      (Sec. 4.2) as an alternative:
+        C_phi = 1/4 sum_j [ D_j(rho u_j phi) + rho D_j(u_j phi) + u_j D_j(rho phi)
+                + phi D_j(rho u_j) + rho u_j D_j phi + rho phi D_j u_j
+                + u_j phi D_j rho ].
   R4  Viscous terms, all in conservative (telescoping) form so that mass,
       momentum and total energy are conserved to round-off on the periodic box:
         momentum i: (mu/Re)[ sum_j D2_j u_i + 1/3 D2_i u_i + 1/3 D_i s_i ],
@@ -79,7 +84,7 @@ class Flow:
     re: float = 1600.0
     pr: float = 0.71
     mu: float = 1.0
-    split: str = "blaisdell"  # or "divergence" (the foil of Sec. 4.2)
+    split: str = "blaisdell"  # "divergence" (the foil of Sec. 4.2) or "kgp" (cubic)
     length: float = 2.0 * math.pi
 
     @property
@@ -163,13 +168,15 @@ def convective(flow: Flow, q: torch.Tensor) -> torch.Tensor:
     (Sec. 2.3.1, Eq. 1).  Blaisdell split (reading R3):
         C_phi = 1/2 sum_j [ D_j(u_j (rho phi)) + u_j D_j(rho phi) + (rho phi) D_j u_j ],
     using rho u_j phi = u_j (rho phi); (rho phi) are the components of Q.
-    Divergence form: C_phi = sum_j D_j(u_j (rho phi))."""
+    Divergence form: C_phi = sum_j D_j(u_j (rho phi)).  KGP cubic form: the
+    seven-term quarter average of reading R3."""
     h = flow.h
     rho = q[0]
     vel = (q[1] / rho, q[2] / rho, q[3] / rho)
     out = []
     for c in range(5):
         f = q[c]  # rho * phi
+        phi = f / rho
         acc = torch.zeros_like(f)
         for j in range(3):
             flux = d1(vel[j] * f, j, h)
@@ -177,6 +184,11 @@ def convective(flow: Flow, q: torch.Tensor) -> torch.Tensor:
                 acc = acc + flux
             elif flow.split == "blaisdell":
                 acc = acc + 0.5 * (flux + vel[j] * d1(f, j, h) + f * d1(vel[j], j, h))
+            elif flow.split == "kgp":
+                m_j = q[1 + j]  # rho u_j
+                acc = acc + 0.25 * (flux + rho * d1(vel[j] * phi, j, h) + vel[j] * d1(f, j, h)
+                                    + phi * d1(m_j, j, h) + m_j * d1(phi, j, h)
+                                    + f * d1(vel[j], j, h) + vel[j] * phi * d1(rho, j, h))
             else:
                 raise ValueError(f"unknown split form {flow.split!r}")
         out.append(acc)

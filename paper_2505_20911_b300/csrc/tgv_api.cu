@@ -71,7 +71,9 @@ static bool valid_dtype(int d) { return d >= TGV_F64 && d <= TGV_F16; }
 static int32_t check(const tgv_config* c) {
   if (!c) return TGV_ERR_ARG;
   if (c->n < 8 || c->n > 1024 || (c->n & 1)) return TGV_ERR_ARG;
-  if (c->split_form != TGV_SPLIT_BLAISDELL && c->split_form != TGV_SPLIT_DIVERGENCE) return TGV_ERR_ARG;
+  if (c->split_form != TGV_SPLIT_BLAISDELL && c->split_form != TGV_SPLIT_DIVERGENCE &&
+      c->split_form != TGV_SPLIT_KGP)
+    return TGV_ERR_ARG;
   if (!valid_dtype(c->q_storage) || !valid_dtype(c->qt_storage) || !valid_dtype(c->compute) ||
       !valid_dtype(c->accumulate))
     return TGV_ERR_ARG;
@@ -249,8 +251,13 @@ static int32_t launch_stage_common(const tgv_config* cfg, const StageArgs& S, bo
   A.zchunk = zc;
   const Problem P = make_problem(*cfg);
   if (ctas) *ctas = stage_ctas(*cfg, tile, zc);
-  cudaError_t e = rhs ? L.rhs[tile](P, A, zc, st)
-                      : (S.diag_part ? L.stage_diag[tile](P, A, zc, st) : L.stage[tile](P, A, zc, st));
+  StageFn fn;
+  if (cfg->split_form == TGV_SPLIT_KGP)
+    fn = rhs ? L.rhs_kgp[tile] : (S.diag_part ? L.stage_kgp_diag[tile] : L.stage_kgp[tile]);
+  else
+    fn = rhs ? L.rhs[tile] : (S.diag_part ? L.stage_diag[tile] : L.stage[tile]);
+  if (!fn) return TGV_ERR_UNSUPPORTED;
+  cudaError_t e = fn(P, A, zc, st);
   return e == cudaSuccess ? TGV_OK : TGV_ERR_CUDA;
 }
 

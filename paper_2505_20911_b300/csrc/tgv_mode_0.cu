@@ -4,7 +4,7 @@
 
 namespace tgv {
 const ModeLaunchers& mode_launchers_0() {
-  static const ModeLaunchers L = make_launchers<double, double, double, double>();
+  static const ModeLaunchers L = make_launchers<double, double, double, double, true>();
   return L;
 }
 }  // namespace tgv

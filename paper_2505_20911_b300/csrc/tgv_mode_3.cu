@@ -4,7 +4,7 @@
 
 namespace tgv {
 const ModeLaunchers& mode_launchers_3() {
-  static const ModeLaunchers L = make_launchers<float, float, float, float>();
+  static const ModeLaunchers L = make_launchers<float, float, float, float, true>();
   return L;
 }
 }  // namespace tgv

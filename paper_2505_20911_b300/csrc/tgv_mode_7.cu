@@ -4,7 +4,7 @@
 
 namespace tgv {
 const ModeLaunchers& mode_launchers_7() {
-  static const ModeLaunchers L = make_launchers<float, __half, float, float>();
+  static const ModeLaunchers L = make_launchers<float, __half, float, float, true>();
   return L;
 }
 }  // namespace tgv

@@ -49,6 +49,8 @@ struct ModeLaunchers {
   StageFn stage[NUM_TILES];      // EPI_RK
   StageFn stage_diag[NUM_TILES]; // EPI_RK with the fused diagnostics of its input
   StageFn rhs[NUM_TILES];        // EPI_RHS
+  // the cubic KGP split (null where a mode does not build it)
+  StageFn stage_kgp[NUM_TILES], stage_kgp_diag[NUM_TILES], rhs_kgp[NUM_TILES];
   OccFn occupancy[NUM_TILES];    // resident CTAs per SM of the EPI_RK kernel
   size_t smem[NUM_TILES];        // dynamic shared memory per CTA
   InitFn init;
@@ -57,9 +59,10 @@ struct ModeLaunchers {
 
 const ModeLaunchers& mode_launchers(int mode);
 
-template <class TS, class TT, class TC, class TA, int TX, int TY, int NP, int EPI, bool DIAG>
+template <class TS, class TT, class TC, class TA, int TX, int TY, int NP, int EPI, bool DIAG,
+          bool KGP = false>
 cudaError_t launch_stage(const Problem& P, const StageArgs& S, int zchunk, cudaStream_t st) {
-  auto kern = stage_kernel<TS, TT, TC, TA, TX, TY, NP, EPI, DIAG>;
+  auto kern = stage_kernel<TS, TT, TC, TA, TX, TY, NP, EPI, DIAG, KGP>;
   const size_t smem = stage_smem_bytes<TS, TT, TC, TX, TY, NP>();
   if (smem > STAGE_SMEM_LIMIT) return cudaErrorInvalidConfiguration;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -102,26 +105,35 @@ cudaError_t launch_diag_partial(const Problem& P, const void* q, double* part, i
   return cudaGetLastError();
 }
 
-template <class TS, class TT, class TC, class TA, int TX, int TY, int NP>
+template <class TS, class TT, class TC, class TA, int TX, int TY, int NP, bool WITH_KGP>
 void set_tile(ModeLaunchers& L, int t) {
   L.stage[t] = launch_stage<TS, TT, TC, TA, TX, TY, NP, EPI_RK, false>;
   L.stage_diag[t] = launch_stage<TS, TT, TC, TA, TX, TY, NP, EPI_RK, true>;
   L.rhs[t] = launch_stage<TS, TT, TC, TA, TX, TY, NP, EPI_RHS, false>;
+  if constexpr (WITH_KGP) {
+    L.stage_kgp[t] = launch_stage<TS, TT, TC, TA, TX, TY, NP, EPI_RK, false, true>;
+    L.stage_kgp_diag[t] = launch_stage<TS, TT, TC, TA, TX, TY, NP, EPI_RK, true, true>;
+    L.rhs_kgp[t] = launch_stage<TS, TT, TC, TA, TX, TY, NP, EPI_RHS, false, true>;
+  } else {
+    L.stage_kgp[t] = L.stage_kgp_diag[t] = L.rhs_kgp[t] = nullptr;
+  }
   L.occupancy[t] = stage_occupancy<TS, TT, TC, TA, TX, TY, NP>;
   L.smem[t] = stage_smem_bytes<TS, TT, TC, TX, TY, NP>();
 }
 
-template <class TS, class TT, class TC, class TA>
+// WITH_KGP: also build the cubic KGP split (the FP64, FP32 and Q FP32 / Qt
+// FP16 modes: the precisions of the paper's split-form study).
+template <class TS, class TT, class TC, class TA, bool WITH_KGP = false>
 ModeLaunchers make_launchers() {
   ModeLaunchers L;
   if constexpr (std::is_same<TC, double>::value) {
-    set_tile<TS, TT, TC, TA, TILE_TX_F64[0], TILE_TY_F64[0], 1>(L, 0);
-    set_tile<TS, TT, TC, TA, TILE_TX_F64[1], TILE_TY_F64[1], 1>(L, 1);
-    set_tile<TS, TT, TC, TA, TILE_TX_F64[2], TILE_TY_F64[2], 1>(L, 2);
+    set_tile<TS, TT, TC, TA, TILE_TX_F64[0], TILE_TY_F64[0], 1, WITH_KGP>(L, 0);
+    set_tile<TS, TT, TC, TA, TILE_TX_F64[1], TILE_TY_F64[1], 1, WITH_KGP>(L, 1);
+    set_tile<TS, TT, TC, TA, TILE_TX_F64[2], TILE_TY_F64[2], 1, WITH_KGP>(L, 2);
   } else {
-    set_tile<TS, TT, TC, TA, TILE_TX[0], TILE_TY[0], 2>(L, 0);
-    set_tile<TS, TT, TC, TA, TILE_TX[1], TILE_TY[1], 2>(L, 1);
-    set_tile<TS, TT, TC, TA, TILE_TX[2], TILE_TY[2], 2>(L, 2);
+    set_tile<TS, TT, TC, TA, TILE_TX[0], TILE_TY[0], 2, WITH_KGP>(L, 0);
+    set_tile<TS, TT, TC, TA, TILE_TX[1], TILE_TY[1], 2, WITH_KGP>(L, 1);
+    set_tile<TS, TT, TC, TA, TILE_TX[2], TILE_TY[2], 2, WITH_KGP>(L, 2);
   }
   L.init = launch_init<TS>;
   L.diag_partial = launch_diag_partial<TS, TC>;

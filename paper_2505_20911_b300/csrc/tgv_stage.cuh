@@ -136,7 +136,31 @@ template <class T> __device__ __forceinline__ T warp_sum(T v) {
 
 // The work of one CTA: the TX x TY column tile at (x0, y0), planes z0 to
 // min(z0 + S.zchunk, n); `cta` indexes its diagnostics partials.
-template <class TS, class TT, class TC, class TA, int TX, int TY, int NP, int EPI, bool DIAG>
+// Extra terms of the cubic KGP split for one direction j (the quarter weights
+// of u_j D f_c and f_c D u_j are shared with the quadratic forms):
+//   kx_c += rho D(u_j phi_c) + phi_c D(rho u_j) + (rho u_j) D phi_c + u_j phi_c D rho
+// with phi = (1, u, v, w, E), E = rho E / rho; raw sums, scaled by 1/12h later.
+template <class V>
+__device__ __forceinline__ void kgp_extra(const int j, const Taps<V>& U, const Taps<V>* Ui,
+                                          const Taps<V>& F0, const Taps<V>& F4, const V* dF,
+                                          const V* fc, const V* uc, const V& c8, V* kx) {
+  const Taps<V> Et = tmul(F4, {rcp(F0.m2), rcp(F0.m1), rcp(F0.p1), rcp(F0.p2)});
+  const V Ec = fc[4] * rcp(fc[0]);
+  const V mj = fc[1 + j];
+  // c = 0 (phi = 1): rho D u_j + D(rho u_j) + u_j D rho
+  kx[0] = kx[0] + fma(fc[0], dsum(U, c8), fma(uc[j], dF[0], dF[1 + j]));
+#pragma unroll
+  for (int c = 1; c < 5; ++c) {
+    const Taps<V>& Ph = (c == 4) ? Et : Ui[c - 1];
+    const V phc = (c == 4) ? Ec : uc[c - 1];
+    const V duphi = dsum(tmul(U, Ph), c8);
+    const V dphi = dsum(Ph, c8);
+    kx[c] = kx[c] + fma(fc[0], duphi, fma(phc, dF[1 + j], fma(mj, dphi, uc[j] * phc * dF[0])));
+  }
+}
+
+template <class TS, class TT, class TC, class TA, int TX, int TY, int NP, int EPI, bool DIAG,
+          bool KGP = false>
 __device__ __forceinline__ void stage_tile(const Problem& P, const StageArgs& S, const int x0,
                                            const int y0, const int z0, const long long cta) {
   using G = Geo<TX, TY, NP>;
@@ -165,9 +189,10 @@ __device__ __forceinline__ void stage_tile(const Problem& P, const StageArgs& S,
   const V c_m30 = V::splat(cvt<TC>(-30.0)), c_2 = V::splat(cvt<TC>(2.0));
   const V c_43 = V::splat(cvt<TC>(4.0 / 3.0)), c_13 = V::splat(cvt<TC>(1.0 / 3.0));
   const V c_m53 = V::splat(cvt<TC>(-5.0 / 3.0)), c_one = V::splat(cvt<TC>(1.0));
+  // convective split: a sum_j D_j(u_j f) + b (sum_j u_j D_j f + f div u) [+ b kx]
   const bool blaisdell = (P.split == TGV_SPLIT_BLAISDELL);
-  const V c_alpha = V::splat(cvt<TC>(blaisdell ? 0.5 : 1.0));
-  const V c_beta = V::splat(cvt<TC>(blaisdell ? 0.5 : 0.0));
+  const V c_alpha = V::splat(cvt<TC>(KGP ? 0.25 : (blaisdell ? 0.5 : 1.0)));
+  const V c_beta = V::splat(cvt<TC>(KGP ? 0.25 : (blaisdell ? 0.5 : 0.0)));
 
   // ---- region units this thread loads and converts each plane.  Unit q < NT
   // is thread q's own tile unit; units q >= NT are the halo (rows 0-1, the
@@ -339,11 +364,11 @@ __device__ __forceinline__ void stage_tile(const Problem& P, const StageArgs& S,
     // shared with the strips).  The partial sums stay in registers across the
     // barrier and phase B adds the x and y directions.
     V fc[5], uc[3], h0c = zero, div = zero;
-    V suf[5], udf[5], d2u[3], ds[3];
+    V suf[5], udf[5], d2u[3], ds[3], kx[5];
     V d2h = zero, dus = zero;
     V grad[3][3];  // grad[i][j] = raw D_j u_i (diagnostics)
 #pragma unroll
-    for (int c = 0; c < 5; ++c) { suf[c] = zero; udf[c] = zero; fc[c] = zero; }
+    for (int c = 0; c < 5; ++c) { suf[c] = zero; udf[c] = zero; fc[c] = zero; kx[c] = zero; }
 #pragma unroll
     for (int i = 0; i < 3; ++i) { d2u[i] = zero; ds[i] = zero; uc[i] = zero; }
     if (k >= z0) {
@@ -378,10 +403,17 @@ __device__ __forceinline__ void stage_tile(const Problem& P, const StageArgs& S,
         const Taps<V>& U = wz;
         const Taps<V> aU = tscale(c_alpha, U);
         const Taps<V> Pt = ztw(F_P, ec);
+        V dFz[5];
+        Taps<V> F0z, F4z;
 #pragma unroll
         for (int c = 0; c < 5; ++c) {
           const Taps<V> F = ztw(c, ec);
           const V dF = dsum(F, c_8);
+          dFz[c] = dF;
+          if constexpr (KGP) {
+            if (c == 0) F0z = F;
+            if (c == 4) F4z = F;
+          }
           udf[c] = fma(uc[2], dF, udf[c]);
           if (c == 0) continue;
           Taps<V> g;
@@ -390,6 +422,10 @@ __device__ __forceinline__ void stage_tile(const Problem& P, const StageArgs& S,
           else g = tmul(aU, F);
           suf[c] = suf[c] + dsum(g, c_8);
           if (c == 3) suf[0] = fma(c_alpha, dF, suf[0]);  // D_z(rho w)
+        }
+        if constexpr (KGP) {
+          const Taps<V> UZall[3] = {uz, vz, wz};
+          kgp_extra(2, U, UZall, F0z, F4z, dFz, fc, uc, c_8, kx);
         }
         const Taps<V>* UZ[3] = {&uz, &vz, &wz};
 #pragma unroll
@@ -453,11 +489,18 @@ __device__ __forceinline__ void stage_tile(const Problem& P, const StageArgs& S,
         const Taps<V> U = tap(F_U + j);
         const Taps<V> aU = tscale(c_alpha, U);
         const Taps<V> Pt = tap(F_P);
+        V dFj[5];
+        Taps<V> F0j, F4j;
         // conserved components: D_j f_c, a D_j(u_j f_c) with merged pressure
 #pragma unroll
         for (int c = 0; c < 5; ++c) {
           const Taps<V> F = tap(c);
           const V dF = dsum(F, c_8);
+          dFj[c] = dF;
+          if constexpr (KGP) {
+            if (c == 0) F0j = F;
+            if (c == 4) F4j = F;
+          }
           udf[c] = fma(uc[j], dF, udf[c]);
           if (c == 0) continue;
           Taps<V> g;
@@ -467,10 +510,14 @@ __device__ __forceinline__ void stage_tile(const Problem& P, const StageArgs& S,
           suf[c] = suf[c] + dsum(g, c_8);
           if (c == 1 + j) suf[0] = fma(c_alpha, dF, suf[0]);  // D_j(rho u_j)
         }
+        Taps<V> Uall[3];
+#pragma unroll
+        for (int i = 0; i < 3; ++i) Uall[i] = (i == j) ? U : tap(F_U + i);
+        if constexpr (KGP) kgp_extra(j, U, Uall, F0j, F4j, dFj, fc, uc, c_8, kx);
         // velocity second derivatives (and first derivatives for diagnostics)
 #pragma unroll
         for (int i = 0; i < 3; ++i) {
-          const Taps<V> Ui = (i == j) ? U : tap(F_U + i);
+          const Taps<V>& Ui = Uall[i];
           const V w8 = (i == j) ? c_43 : c_one;
           d2u[i] = fma(w8, d2sum(Ui, uc[i], c_16, c_m30), d2u[i]);
           if constexpr (DIAG) grad[i][j] = dsum(Ui, c_8);
@@ -500,7 +547,7 @@ __device__ __forceinline__ void stage_tile(const Problem& P, const StageArgs& S,
       V R[5];
 #pragma unroll
       for (int c = 0; c < 5; ++c)
-        R[c] = -(fma(c_inv12h, fma(c_beta, udf[c], suf[c]), c_beta * fc[c] * div));
+        R[c] = -(fma(c_inv12h, fma(c_beta, udf[c] + kx[c], suf[c]), c_beta * fc[c] * div));
 #pragma unroll
       for (int i = 0; i < 3; ++i)
         R[1 + i] = fma(c_nu, fma(c_inv12h2, d2u[i], c_13 * c_inv12h * ds[i]), R[1 + i]);
@@ -582,12 +629,13 @@ __device__ __forceinline__ void stage_tile(const Problem& P, const StageArgs& S,
   }
 }
 
-template <class TS, class TT, class TC, class TA, int TX, int TY, int NP, int EPI, bool DIAG>
+template <class TS, class TT, class TC, class TA, int TX, int TY, int NP, int EPI, bool DIAG,
+          bool KGP = false>
 __global__ void __launch_bounds__(Geo<TX, TY, NP>::NT, 1)
 stage_kernel(const Problem P, const StageArgs S) {
   const long long cta = ((long long)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
-  stage_tile<TS, TT, TC, TA, TX, TY, NP, EPI, DIAG>(P, S, blockIdx.x * TX, blockIdx.y * TY,
-                                                    blockIdx.z * S.zchunk, cta);
+  stage_tile<TS, TT, TC, TA, TX, TY, NP, EPI, DIAG, KGP>(P, S, blockIdx.x * TX, blockIdx.y * TY,
+                                                         blockIdx.z * S.zchunk, cta);
 }
 
 }  // namespace tgv

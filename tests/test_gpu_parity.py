@@ -43,7 +43,7 @@ def test_rhs_fp64_matches_oracle(tile, n, field):
     assert max(err) < 1e-11, err
 
 
-@pytest.mark.parametrize("split", ["blaisdell", "divergence"])
+@pytest.mark.parametrize("split", ["blaisdell", "divergence", "kgp"])
 @pytest.mark.parametrize("zchunk", [0, 5, 16])
 def test_rhs_split_forms_and_zchunks(split, zchunk):
     cfg = tgv.Config(n=32, mode="fp64", split=split, zchunk=zchunk, mach=0.3, re=50.0)
@@ -165,3 +165,28 @@ def test_full_size_half_single_stage_sampled(n):
     mag = torch.tensor([4.0, big + 4, big + 4, big + 4, big + 4], dtype=torch.float64)
     bound = 4 * dt * 2.0 ** -24 * mag * 1.5 / h
     assert bool(((got - ref).abs() <= 2.0 ** -10 * ref.abs() + bound).all())
+
+
+@pytest.mark.parametrize("n,tile", [(32, 0), (40, 0), (48, 3)])
+def test_kgp_rhs_and_steps_match_oracle(n, tile):
+    """The cubic KGP split (FP64): residual on a random state, and 5 RK3 steps."""
+    cfg = tgv.Config(n=n, mode="fp64", split="kgp", mach=0.3, re=100.0, tile=tile)
+    flow = oracle_flow(cfg)
+    q64 = random_state(cfg, seed=17 + n)
+    r = torch.empty(5, n, n, n, dtype=torch.float64, device="cuda")
+    tgv.rhs_eval(cfg, encode(cfg, q64), r)
+    assert max(max_rel(r.cpu(), oracle.residual(flow, q64))) < 1e-11
+    qa = encode(cfg, q64)
+    qb, qt = torch.empty_like(qa), tgv.empty_qt(cfg)
+    par = tgv.rk_step(cfg, qa, qb, qt, 0.002, 5)
+    ref = oracle.run(flow, q64, 0.002, 5)
+    assert max(rel_l2((qb if par else qa).cpu(), ref)) < 1e-12
+
+
+def test_kgp_unsupported_where_not_built():
+    cfg = tgv.Config(n=32, mode="fp16_fp32", split="kgp")
+    q = tgv.empty_state(cfg)
+    r = torch.empty(5, 32, 32, 32, dtype=torch.float32, device="cuda")
+    with pytest.raises(tgv.TGVError) as ei:
+        tgv.rhs_eval(cfg, q, r)
+    assert ei.value.status == tgv._abi.TGV_ERR_UNSUPPORTED

@@ -98,11 +98,12 @@ def test_residual_converges_at_fourth_order(exact, group):
         assert a / b > 13.0, (group, c, a, b)
 
 
-def test_divergence_form_converges_to_same_rhs(exact):
+@pytest.mark.parametrize("split", ["divergence", "kgp"])
+def test_other_split_forms_converge_to_same_rhs(exact, split):
     prim_fns, conv_fns, _, _ = exact
     errs = []
     for n in (32, 64):
-        flow = oracle.Flow(n=n, gamma=GAMMA, mach=MACH, re=RE, pr=PR, split="divergence")
+        flow = oracle.Flow(n=n, gamma=GAMMA, mach=MACH, re=RE, pr=PR, split=split)
         q = oracle.conserved(flow, *_eval(prim_fns, n))
         ref = torch.stack(_eval(conv_fns, n))
         errs.append(float((oracle.convective(flow, q) - ref).abs().max()))
@@ -116,7 +117,7 @@ def _random_state(n, seed, mach=0.3):
     return flow, oracle.conserved(flow, rho, u, v, w, p)
 
 
-@pytest.mark.parametrize("split", ["blaisdell", "divergence"])
+@pytest.mark.parametrize("split", ["blaisdell", "divergence", "kgp"])
 def test_discrete_conservation(split):
     flow, q = _random_state(16, 3)
     flow = flow.with_(split=split)
@@ -171,3 +172,20 @@ def test_residual_keeps_tgv_symmetries():
     for op in _tgv_symmetry_ops(flow.n):
         assert torch.allclose(op(q), q, rtol=0, atol=1e-13 * float(q.abs().max()))
         assert torch.allclose(op(r), r, rtol=0, atol=1e-12 * float(r.abs().max()))
+
+
+def test_kgp_kinetic_energy_identity():
+    """The cubic KGP split makes the convective transport of kinetic energy a
+    telescoping sum: sum_x [u_i C_(rho u_i) - |u|^2/2 C_rho] = 0 (a discrete
+    property of the form; the Blaisdell and divergence forms do not have it)."""
+    flow, q = _random_state(16, 9)
+    rho = q[0]
+    u = [q[1 + i] / rho for i in range(3)]
+    ke = 0.5 * (u[0] ** 2 + u[1] ** 2 + u[2] ** 2)
+
+    def imbalance(split):
+        conv = oracle.convective(flow.with_(split=split), q)
+        s = sum(u[i] * conv[1 + i] for i in range(3)) - ke * conv[0]
+        return abs(float(s.sum())) / float((u[0] * conv[1]).abs().sum())
+    assert imbalance("kgp") < 1e-13, imbalance("kgp")
+    assert imbalance("blaisdell") > 1e-6 and imbalance("divergence") > 1e-6
