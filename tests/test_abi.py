@@ -113,3 +113,11 @@ def test_adjoint_entry_points_validate_on_host():
                                  None) == _abi.TGV_ERR_ARG
     assert lib.tgv_grad_final_ke(C.byref(c64), fake, 1.0, 10, 5, fake, fake, fake, 1 << 40,
                                  None) == _abi.TGV_ERR_UNSTABLE_DT
+
+
+def test_missing_library_fails_loudly(monkeypatch):
+    """No fallback: without libtgv.so the binding raises instead of computing."""
+    monkeypatch.setattr(_abi, "_lib", None)
+    monkeypatch.setattr(_abi, "LIB_PATH", os.path.join(ROOT, "no_such_dir", "libtgv.so"))
+    with pytest.raises(ImportError):
+        _abi.lib()

@@ -1,0 +1,49 @@
+"""The host-buffer entry point and the workspace / argument errors of the C ABI
+on a device."""
+import pytest
+import torch
+
+import paper_2505_20911_b300 as tgv
+from paper_2505_20911_b300 import _abi
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.mark.parametrize("mode", ["fp64", "fp16_fp32"])
+def test_run_host_matches_device_path_bitwise(mode):
+    cfg = tgv.Config(n=48, mode=mode, encoding="offset" if mode == "fp16_fp32" else "plain")
+    q0 = tgv.empty_state(cfg)
+    tgv.tgv_init(cfg, q0)
+    # device path
+    qa, qb, qt = q0.clone(), torch.empty_like(q0), tgv.empty_qt(cfg)
+    diag = torch.empty(3, tgv.TGV_DIAG_COUNT, dtype=torch.float64, device="cuda")
+    par = tgv.rk_step(cfg, qa, qb, qt, 0.004, 10, 5, diag, tgv.empty_workspace(cfg))
+    ref = (qb if par else qa).cpu()
+    # host path: pinned host in/out, device workspace from the caller
+    h_in = q0.cpu().pin_memory()
+    h_out = torch.empty_like(h_in).pin_memory()
+    d_host = torch.empty(3 * tgv.TGV_DIAG_COUNT, dtype=torch.float64).pin_memory()
+    ws = torch.empty(tgv.tgv_run_host_workspace_bytes(cfg, 10, 5), dtype=torch.uint8, device="cuda")
+    tgv.tgv_run_host(cfg, h_in, h_out, 0.004, 10, 5, d_host, ws)
+    assert torch.equal(h_out, ref)
+    assert torch.equal(d_host.view(3, -1), diag.cpu())
+
+
+def test_workspace_errors():
+    cfg = tgv.Config(n=32)
+    q = tgv.empty_state(cfg)
+    tgv.tgv_init(cfg, q)
+    out = torch.empty(tgv.TGV_DIAG_COUNT, dtype=torch.float64, device="cuda")
+    small = torch.empty(8, dtype=torch.uint8, device="cuda")
+    with pytest.raises(tgv.TGVError) as ei:
+        tgv.diagnostics_reduce(cfg, q, out, small)
+    assert ei.value.status == _abi.TGV_ERR_WORKSPACE
+    qb, qt = torch.empty_like(q), tgv.empty_qt(cfg)
+    diag = torch.empty(2, tgv.TGV_DIAG_COUNT, dtype=torch.float64, device="cuda")
+    with pytest.raises(tgv.TGVError) as ei:
+        tgv.rk_step(cfg, q, qb, qt, 0.004, 1, 1, diag, small)
+    assert ei.value.status == _abi.TGV_ERR_WORKSPACE
+    with pytest.raises(tgv.TGVError) as ei:
+        tgv.rk_step(cfg, q, qb, qt, 0.05, 1)           # above the stability limit
+    assert ei.value.status == _abi.TGV_ERR_UNSTABLE_DT
+    tgv.rk_step(cfg.with_(allow_unstable_dt=True), q, qb, qt, 0.02, 1)  # allowed when asked
