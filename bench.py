@@ -447,6 +447,29 @@ def extra_workloads(args, tgv, torch, dev, stream, peaks):
     big["fp16_vs_fp32"] = big["fp16_fp32"]["value"] / big["fp32"]["value"]
     out["n512"] = big
 
+    # the paper's own workload: TGSym 256^3 (pi^3 box with mirror planes),
+    # M = 0.5, Re = 800, dt = 0.0025; ms per iteration (one RK3 step) per mode,
+    # beside the paper's A100 Storesome times (context, other hardware)
+    paper_ms = {"fp64": 50.31, "spdp": 37.60, "fp32": 25.00, "fp16": 18.67}
+    tgs = {}
+    for mode in ("fp64", "spdp", "fp32", "hpsp", "fp16_fp32", "fp16"):
+        cfg = tgv.Config(n=256, mode=mode, length=math.pi, symmetric=True, mach=0.5, re=800.0,
+                         encoding="offset" if mode in OFFSET_MODES else "plain")
+        qa = tgv.empty_state(cfg, dev)
+        qb, qt = torch.empty_like(qa), tgv.empty_qt(cfg, dev)
+        tgv.tgv_init(cfg, qa)
+        tgv.rk_step(cfg, qa, qb, qt, 0.0025, 2, 0, None, None, stream)
+        steps = 4 if mode == "fp64" else 20
+        ms = ev_time(lambda: tgv.rk_step(cfg, qa, qb, qt, 0.0025, steps, 0, None, None, stream))
+        rec = {"ms_per_iteration": ms / steps, "value": 256 ** 3 * steps / (ms * 1e-3)}
+        if mode in paper_ms:
+            rec["paper_a100_storesome_ms"] = paper_ms[mode]
+            rec["speedup_vs_paper_a100"] = paper_ms[mode] / rec["ms_per_iteration"]
+        tgs[mode] = rec
+        del qa, qb, qt
+        torch.cuda.empty_cache()
+    out["tgsym_256"] = tgs
+
     # adjoint: 64^3, 200 steps, checkpoint every 20
     adj = {}
     for mode in ("fp64", "fp32"):
@@ -589,7 +612,7 @@ def main():
                 config=config, roofline=res["roofline"], e2e=res["e2e"],
                 gpu_launches=res["gpu_launches"], clocks=res["clocks"], modes=res["modes"],
                 diag_last=res["diag_last"])
-    for key in ("n512", "adjoint_64", "ensemble_48"):
+    for key in ("n512", "tgsym_256", "adjoint_64", "ensemble_48"):
         if key in res:
             line[key] = res[key]
     if world == 1 and not args.no_cpu:

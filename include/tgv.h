@@ -67,6 +67,15 @@ typedef enum { TGV_ENC_PLAIN = 0, TGV_ENC_OFFSET = 1 } tgv_encoding;
                                          synchronise the stream and stop with
                                          TGV_ERR_NONFINITE if the state holds a
                                          NaN or Inf (costs one sync per record) */
+#define TGV_FLAG_CELL_CENTERED 4      /* grid points at (i + 1/2) L/N            */
+#define TGV_FLAG_SYMMETRIC 8          /* the symmetric box of Sec. 4.1 (TGSym):
+                                         [0, L]^3, cell-centred, every face a
+                                         mirror plane (ghost i -> -1-i and
+                                         2N-1-i, the momentum component normal
+                                         to the face odd, the rest even).  With
+                                         L = pi it holds one octant of the
+                                         periodic 2pi problem with 2N points.
+                                         Not supported by the adjoint. */
 
 /*
  * One TGV problem.  Physics follows Sec. 3.1 / Sec. 4.1 (nondimensional):
@@ -129,7 +138,9 @@ double tgv_dt_max(const tgv_config* cfg);
 
 /*
  * Taylor-Green initial condition (Sec. 4.1, Eqs. 6-10) into q (device, Q
- * layout, q_storage, encoded).  Evaluated in FP64 on the device, then rounded.
+ * layout, q_storage, encoded), at the grid points i*h, or (i + 1/2)*h with
+ * TGV_FLAG_CELL_CENTERED or TGV_FLAG_SYMMETRIC.  Evaluated in FP64 on the
+ * device, then rounded.
  */
 int32_t tgv_init(const tgv_config* cfg, void* q, void* stream);
 

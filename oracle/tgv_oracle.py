@@ -51,6 +51,12 @@ used):
       and a mixed second derivative is D_i applied after D_j.
   R5  Constant viscosity mu (1 by default, 0 for the inviscid limit), Pr = 0.71.
   R8  eps^S is normalised as a volume average, like K: eps^S = <omega.omega>/Re.
+  R13 The symmetric box of Sec. 4.1 (TGSym, [0, L]^3 with symmetry planes on
+      every face): cell-centred points x_i = (i + 1/2) h, h = L/N, ghosts by
+      mirroring about the faces, the velocity component normal to a face odd
+      and everything else even.  This is exactly the restriction to the first
+      octant of the periodic problem on [0, 2L)^3 with 2N cell-centred points
+      whose state is the mirror extension, and that is how it is computed here.
 
 Array layout: a field is a float64 tensor of shape (N, N, N) indexed
 [z, y, x] (x fastest, matching the device layout idx = (k*N + j)*N + i); the
@@ -86,6 +92,8 @@ class Flow:
     mu: float = 1.0
     split: str = "blaisdell"  # "divergence" (the foil of Sec. 4.2) or "kgp" (cubic)
     length: float = 2.0 * math.pi
+    offset: float = 0.0       # grid points at (i + offset) h; 0.5 = cell-centred
+    symmetric: bool = False   # symmetry planes on every face (reading R13)
 
     @property
     def h(self) -> float:
@@ -121,9 +129,9 @@ def d2(f: torch.Tensor, axis: int, h: float) -> torch.Tensor:
             + 16.0 * shift(f, axis, -1) - shift(f, axis, -2)) / (12.0 * h * h)
 
 
-def grid(n: int, length: float = 2.0 * math.pi):
-    """Coordinates (z, y, x) of the N^3 grid, each broadcast to (N, N, N)."""
-    c = torch.arange(n, dtype=F64) * (length / n)
+def grid(n: int, length: float = 2.0 * math.pi, offset: float = 0.0):
+    """Coordinates (x, y, z) of the N^3 grid points (i + offset) L/N, each (N, N, N)."""
+    c = (torch.arange(n, dtype=F64) + offset) * (length / n)
     z, y, x = torch.meshgrid(c, c, c, indexing="ij")
     return x, y, z
 
@@ -150,7 +158,7 @@ def initial_condition(flow: Flow) -> torch.Tensor:
     """Taylor-Green initial field, Sec. 4.1, Eqs. 6-10:
     u = sin x cos y cos z, v = -cos x sin y cos z, w = 0,
     p = 1/(gamma M^2) + (cos 2x + cos 2y)(2 + cos 2z)/16, rho = gamma M^2 p."""
-    x, y, z = grid(flow.n, flow.length)
+    x, y, z = grid(flow.n, flow.length, 0.5 if flow.symmetric else flow.offset)
     u = torch.sin(x) * torch.cos(y) * torch.cos(z)
     v = -torch.cos(x) * torch.sin(y) * torch.cos(z)
     w = torch.zeros_like(u)
@@ -234,8 +242,27 @@ def viscous_terms(flow: Flow, q: torch.Tensor) -> torch.Tensor:
     return torch.stack([zero, mom[0], mom[1], mom[2], nu * work + heat])
 
 
+def mirror_extend(q: torch.Tensor) -> torch.Tensor:
+    """(5, N, N, N) state of the symmetric box -> (5, 2N, 2N, 2N) periodic state:
+    along each axis the second half is the mirror image of the first, with the
+    momentum component normal to that axis negated (reading R13)."""
+    out = q
+    for axis, dim in ((0, 3), (1, 2), (2, 1)):
+        m = torch.flip(out, dims=[dim]).clone()
+        m[1 + axis] = -m[1 + axis]
+        out = torch.cat([out, m], dim=dim)
+    return out
+
+
+def _periodic_twin(flow: Flow) -> Flow:
+    return flow.with_(n=2 * flow.n, length=2 * flow.length, offset=0.5, symmetric=False)
+
+
 def residual(flow: Flow, q: torch.Tensor) -> torch.Tensor:
     """R(Q) = dQ/dt = -C - (pressure terms) + (viscous and heat terms)."""
+    if flow.symmetric:
+        n = flow.n
+        return residual(_periodic_twin(flow), mirror_extend(q))[:, :n, :n, :n]
     r = -convective(flow, q) - pressure_terms(flow, q)
     if flow.mu != 0.0:
         r = r + viscous_terms(flow, q)
@@ -281,6 +308,9 @@ DIAG_NAMES = ("K", "K_rho", "enstrophy", "eps_S", "rho", "rho_u", "rho_v",
 
 
 def vorticity(flow: Flow, q):
+    if flow.symmetric:
+        n = flow.n
+        return tuple(c[:n, :n, :n] for c in vorticity(_periodic_twin(flow), mirror_extend(q)))
     h = flow.h
     _, u, v, w, _, _ = primitives(flow, q)
     wx = d1(w, 1, h) - d1(v, 2, h)

@@ -56,6 +56,8 @@ class Config:
     zchunk: int = 0
     allow_unstable_dt: bool = False
     check_finite: bool = False
+    cell_centered: bool = False
+    symmetric: bool = False      # the symmetric box (TGSym); set length = pi
     length: float = 2.0 * math.pi
 
     def with_(self, **kw) -> "Config":
@@ -83,7 +85,9 @@ class Config:
             encoding={"plain": TGV_ENC_PLAIN, "offset": TGV_ENC_OFFSET}[self.encoding],
             tile=self.tile, zchunk=self.zchunk,
             flags=(TGV_FLAG_ALLOW_UNSTABLE_DT if self.allow_unstable_dt else 0)
-            | (_abi.TGV_FLAG_CHECK_FINITE if self.check_finite else 0),
+            | (_abi.TGV_FLAG_CHECK_FINITE if self.check_finite else 0)
+            | (_abi.TGV_FLAG_CELL_CENTERED if self.cell_centered else 0)
+            | (_abi.TGV_FLAG_SYMMETRIC if self.symmetric else 0),
             length=self.length, gamma=self.gamma, mach=self.mach, re=self.re, pr=self.pr,
             mu=self.mu)
 

@@ -20,6 +20,8 @@ TGV_SPLIT_BLAISDELL, TGV_SPLIT_DIVERGENCE, TGV_SPLIT_KGP = 0, 1, 2
 TGV_ENC_PLAIN, TGV_ENC_OFFSET = 0, 1
 TGV_FLAG_ALLOW_UNSTABLE_DT = 1
 TGV_FLAG_CHECK_FINITE = 2
+TGV_FLAG_CELL_CENTERED = 4
+TGV_FLAG_SYMMETRIC = 8
 TGV_DIAG_COUNT = 10
 TGV_ABI_VERSION = 1
 

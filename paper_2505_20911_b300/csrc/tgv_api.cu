@@ -54,6 +54,8 @@ Problem make_problem(const tgv_config& c) {
   }
   P.mach = c.mach;
   P.re = c.re;
+  P.symmetric = (c.flags & TGV_FLAG_SYMMETRIC) ? 1 : 0;
+  P.offset = (c.flags & (TGV_FLAG_SYMMETRIC | TGV_FLAG_CELL_CENTERED)) ? 0.5 : 0.0;
   return P;
 }
 

@@ -89,7 +89,24 @@ struct Problem {
   double kappa;     // mu/((gamma-1) M^2 Pr Re)
   double rho0, rhoE0;      // encoding offsets (0 for TGV_ENC_PLAIN)
   double mach, re;
+  double offset;    // grid points at (i + offset) h: 0, or 0.5 (cell-centred)
+  int symmetric;    // 1: mirror planes on every face (TGV_FLAG_SYMMETRIC)
 };
+
+// Grid index of a neighbour at i (possibly outside [0, n)) and whether the
+// mirror flipped it: periodic wrap, or reflection about the faces of the
+// cell-centred symmetric box (i -> -1-i, i -> 2n-1-i).  Indices more than one
+// box length outside are clamped (they only feed points outside the grid).
+__host__ __device__ __forceinline__ int wrap_index(int i, int n, bool symmetric, bool* flipped) {
+  *flipped = false;
+  if (!symmetric) {
+    i %= n;
+    return i < 0 ? i + n : i;
+  }
+  if (i < 0) { i = -1 - i; *flipped = true; }
+  else if (i >= n) { i = 2 * n - 1 - i; *flipped = true; }
+  return i < 0 ? 0 : (i >= n ? n - 1 : i);
+}
 
 Problem make_problem(const tgv_config& c);
 

@@ -13,7 +13,7 @@ __global__ void init_kernel(const Problem P, TS* __restrict__ q) {
   for (long long o = blockIdx.x * (long long)blockDim.x + threadIdx.x; o < n3;
        o += (long long)gridDim.x * blockDim.x) {
     const int i = (int)(o % n), j = (int)((o / n) % n), k = (int)(o / nn);
-    const double x = i * P.h, y = j * P.h, z = k * P.h;
+    const double x = (i + P.offset) * P.h, y = (j + P.offset) * P.h, z = (k + P.offset) * P.h;
     double sx, cx, sy, cy, sz, cz;
     sincos(x, &sx, &cx);
     sincos(y, &sy, &cy);
@@ -92,10 +92,10 @@ diag_partial_kernel(const Problem P, const TS* __restrict__ q, double* __restric
       for (int tt = 0; tt < 4; ++tt) {
         int xi = i, yj = j, zk = k;
         int* c = (b == 0) ? &xi : (b == 1) ? &yj : &zk;
-        *c += off[tt];
-        if (*c < 0) *c += n;
-        if (*c >= n) *c -= n;
+        bool flipped;
+        *c = wrap_index(*c + off[tt], n, P.symmetric != 0, &flipped);
         load_vel<TS, DT>(q, (long long)zk * nn + (long long)yj * n + xi, n3, rho0, dst[tt]);
+        if (flipped) dst[tt][b] = -dst[tt][b];  // mirror ghost: normal velocity odd
       }
 #pragma unroll
       for (int a = 0; a < 3; ++a) g[a][b] = s * (DT(8) * (up1[a] - um1[a]) - (up2[a] - um2[a]));

@@ -201,12 +201,14 @@ __device__ __forceinline__ void stage_tile(const Problem& P, const StageArgs& S,
   using RawT = typename UnitIO<TA, NP, TT>::Raw;
   RawS* stage_q = reinterpret_cast<RawS*>(strips + NSTRIP * PL);       // [5][PLU]
   RawT* stage_t = reinterpret_cast<RawT*>(stage_q + 5 * PLU);         // [2][5][NT]
-  int goff[PERU], eoff[PERU];
+  int goff[PERU], eoff[PERU], tform[PERU];  // tform: 1 swap lanes, 2 -rho u, 4 -rho v
+  const bool sym = P.symmetric != 0;
 #pragma unroll
   for (int r = 0; r < PERU; ++r) {
     const int q = tid + r * NT;
     goff[r] = -1;
     eoff[r] = 0;
+    tform[r] = 0;
     if (q < PLU) {
       int rx, ry;
       if (q < NT) {
@@ -226,19 +228,23 @@ __device__ __forceinline__ void stage_tile(const Problem& P, const StageArgs& S,
           rx = (h % RXU) * NP;
         }
       }
-      int gx = x0 - 2 + rx;
-      gx = gx < 0 ? gx + n : (gx >= n ? gx % n : gx);
-      int gy = y0 - 2 + ry;
-      gy = gy < 0 ? gy + n : (gy >= n ? gy % n : gy);
+      int gx = x0 - 2 + rx, gy = y0 - 2 + ry;
+      bool fx = false, fy = false;
+      // a unit starts at an even x and n is even, so it never straddles a face;
+      // mirrored, its last point lands first: load from the mirror of that one
+      gx = wrap_index(gx + (sym ? NP - 1 : 0), n, sym, &fx);
+      if (!fx && sym) gx -= NP - 1;
+      gy = wrap_index(gy, n, sym, &fy);
       goff[r] = gy * n + gx;
       eoff[r] = ry * RX + rx;
+      tform[r] = (fx && NP == 2 ? 1 : 0) | (fx ? 2 : 0) | (fy ? 4 : 0);
     }
   }
   const long long tile_off = (long long)(y0 + ty) * n + (x0 + NP * tx);
   const bool active_xy = (x0 + NP * tx < n) && (y0 + ty < n);
   auto prefetch = [&](int zl) {  // cp.async of raw plane zl into the staging
-    int zw = zl % n;
-    if (zw < 0) zw += n;
+    bool fz;
+    const int zw = wrap_index(zl, n, sym, &fz);
     const long long zoff = (long long)zw * nn;
 #pragma unroll
     for (int r = 0; r < PERU; ++r) {
@@ -259,8 +265,10 @@ __device__ __forceinline__ void stage_tile(const Problem& P, const StageArgs& S,
       cp_async<sizeof(RawT)>(dst + c * NT + tid, qt + (long long)kq * nn + tile_off + c * n3);
   };
   RawS qin_q[3][5];  // raw Q of the own unit at planes zl, zl-1, zl-2
-  auto commit = [&](int slot) {  // staged raw plane -> primitives in the ring
+  auto commit = [&](int slot, int zl) {  // staged raw plane -> primitives in the ring
     TC* base = ring + slot * NFLD * PL;
+    bool fz;
+    wrap_index(zl, n, sym, &fz);
 #pragma unroll
     for (int r = 0; r < PERU; ++r) {
       const int q = tid + r * NT;
@@ -277,9 +285,19 @@ __device__ __forceinline__ void stage_tile(const Problem& P, const StageArgs& S,
           }
         }
         const int e = eoff[r];
-        const V rho = IO::conv(raw[0]) + c_rho0;
-        const V ru = IO::conv(raw[1]), rv = IO::conv(raw[2]), rw = IO::conv(raw[3]);
-        const V rE = IO::conv(raw[4]) + c_rhoE0;
+        V rho = IO::conv(raw[0]) + c_rho0;
+        V ru = IO::conv(raw[1]), rv = IO::conv(raw[2]), rw = IO::conv(raw[3]);
+        V rE = IO::conv(raw[4]) + c_rhoE0;
+        if (sym) {  // ghost of the symmetric box: mirror image, normal momentum odd
+          const int tf = tform[r];
+          if (tf & 1) {
+            rho = rho.swapped(); ru = ru.swapped(); rv = rv.swapped();
+            rw = rw.swapped(); rE = rE.swapped();
+          }
+          if (tf & 2) ru = -ru;
+          if (tf & 4) rv = -rv;
+          if (fz) rw = -rw;
+        }
         const V ri = rcp(rho);
         const V uu = ru * ri, vv = rv * ri, ww = rw * ri;
         const V ke = c_half * fma(ru, uu, fma(rv, vv, rw * ww));
@@ -336,7 +354,7 @@ __device__ __forceinline__ void stage_tile(const Problem& P, const StageArgs& S,
   for (int zl = zbase; zl < z1 + 2; ++zl) {
     const int slot = (zl - zbase) % NSLOT;
     cp_async_wait<0>();
-    commit(slot);
+    commit(slot, zl);
     __syncthreads();
     // next plane and, for the next centre plane, this unit's Qt (one group)
     if (zl + 1 < z1 + 2) prefetch(zl + 1);

@@ -23,6 +23,7 @@ template <class T> struct Vec<T, 1> {
   __device__ __forceinline__ T get(int) const { return v; }
   // (a.hi, b.lo) of two consecutive units; for one-point units it is b
   static __device__ __forceinline__ Vec mix(const Vec&, const Vec& b) { return b; }
+  __device__ __forceinline__ Vec swapped() const { return *this; }
 };
 template <class T> __device__ __forceinline__ Vec<T, 1> operator+(Vec<T, 1> a, Vec<T, 1> b) { return Vec<T, 1>(a.v + b.v); }
 template <class T> __device__ __forceinline__ Vec<T, 1> operator-(Vec<T, 1> a, Vec<T, 1> b) { return Vec<T, 1>(a.v - b.v); }
@@ -50,6 +51,7 @@ template <> struct Vec<float, 2> {
   __device__ __forceinline__ void store(float* p) const { *reinterpret_cast<float2*>(p) = v; }
   __device__ __forceinline__ float get(int e) const { return e ? v.y : v.x; }
   static __device__ __forceinline__ Vec mix(const Vec& a, const Vec& b) { return Vec(a.v.y, b.v.x); }
+  __device__ __forceinline__ Vec swapped() const { return Vec(v.y, v.x); }
 };
 __device__ __forceinline__ Vec<float, 2> operator+(Vec<float, 2> a, Vec<float, 2> b) {
   return Vec<float, 2>(__fadd2_rn(a.v, b.v));
@@ -83,6 +85,7 @@ template <> struct Vec<__half, 2> {
   static __device__ __forceinline__ Vec mix(const Vec& a, const Vec& b) {
     return Vec(__halves2half2(__high2half(a.v), __low2half(b.v)));
   }
+  __device__ __forceinline__ Vec swapped() const { return Vec(__lowhigh2highlow(v)); }
 };
 __device__ __forceinline__ Vec<__half, 2> operator+(Vec<__half, 2> a, Vec<__half, 2> b) { return Vec<__half, 2>(__hadd2(a.v, b.v)); }
 __device__ __forceinline__ Vec<__half, 2> operator-(Vec<__half, 2> a, Vec<__half, 2> b) { return Vec<__half, 2>(__hsub2(a.v, b.v)); }

@@ -11,7 +11,9 @@ import paper_2505_20911_b300 as tgv
 
 def oracle_flow(cfg: tgv.Config) -> oracle.Flow:
     return oracle.Flow(n=cfg.n, gamma=cfg.gamma, mach=cfg.mach, re=cfg.re, pr=cfg.pr,
-                       mu=cfg.mu, split=cfg.split, length=cfg.length)
+                       mu=cfg.mu, split=cfg.split, length=cfg.length,
+                       offset=0.5 if (cfg.cell_centered or cfg.symmetric) else 0.0,
+                       symmetric=cfg.symmetric)
 
 
 def offsets(cfg: tgv.Config):
