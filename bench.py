@@ -53,7 +53,11 @@ def parse():
     ap.add_argument("--accuracy", action="store_true",
                     help="precision sweep accuracy report (--n, --accuracy-steps) against "
                          "the FP64 GPU path; prints one JSON object")
-    ap.add_argument("--accuracy-steps", type=int, default=2000)
+    ap.add_argument("--accuracy-steps", type=int, default=None,
+                    help="default: 2000 (tgv), 8000 = t 20 (tgsym)")
+    ap.add_argument("--accuracy-workload", default="tgv", choices=["tgv", "tgsym"],
+                    help="tgv: periodic 2 pi box, M 0.1, Re 1600, dt 0.00125 at 256^3; tgsym: "
+                         "the symmetric pi box of Sec. 4.1/4.3, M 0.5, Re 800, dt 0.0025")
     ap.add_argument("--profile-case", default=None, metavar="MODE",
                     help="run 2 warm-up RK3 steps and 1 more step of MODE at --n, then exit "
                          "(the small case an ncu capture of the stage kernel uses)")
@@ -76,22 +80,29 @@ def profile_case(args):
 
 
 def accuracy_sweep(args):
-    """Every mode of the sweep at --n for --accuracy-steps steps (dt = 0.00125
-    scaled to the grid), K and enstrophy logged every 10 steps in FP64, against
-    the FP64 GPU path (which the tests pin to the FP64 oracle).  Errors: field
-    relative L2 at the end (rho, momentum vector, rho E), the dissipation rate
-    -dK/dt from central differences of K (max error / max |ref|), the
-    solenoidal dissipation eps^S(t) (max error / max ref) and the mean
-    absolute eps^S difference at every 0.5 time units relative to the mean
-    eps^S there."""
+    """Every mode of the sweep at --n for --accuracy-steps steps, K and
+    enstrophy logged every 10 steps in FP64, against the FP64 GPU path (which
+    the tests pin to the FP64 oracle).  Workloads: the periodic TGV (dt =
+    0.00125 scaled to the grid) or the symmetric TGSym box at the paper's
+    M = 0.5, Re = 800, dt = 0.0025 (to t = 20 by default, the paper's full
+    run).  Errors: field relative L2 at the end (rho, momentum vector, rho E),
+    the dissipation rate -dK/dt from central differences of K (max error / max
+    |ref|), the solenoidal dissipation eps^S(t) (max error / max ref), and the
+    paper's measure of Sec. 4.2: the mean absolute difference of the
+    dissipation at every 0.5 time units, absolute and relative to the mean
+    reference value there, for eps^S and -dK/dt."""
     import torch
     import paper_2505_20911_b300 as tgv
-    n, steps = args.n, args.accuracy_steps
-    dt = DT_DEFAULT * 256.0 / n
+    sym = args.accuracy_workload == "tgsym"
+    n = args.n
+    steps = args.accuracy_steps or (8000 if sym else 2000)
+    dt = 0.0025 if sym else DT_DEFAULT * 256.0 / n
     nrec = steps // DIAG_EVERY + 1
 
     def run(mode, encoding=None):
         cfg = mode_config(tgv, n, mode)
+        if sym:
+            cfg = cfg.with_(length=math.pi, symmetric=True, mach=0.5, re=800.0)
         if encoding:
             cfg = cfg.with_(encoding=encoding)
         qa = tgv.empty_state(cfg)
@@ -115,9 +126,13 @@ def accuracy_sweep(args):
     diss = lambda K: [-(K[i + 1] - K[i - 1]) / (2 * DIAG_EVERY * dt) for i in range(1, len(K) - 1)]
     d_ref = diss(K_ref)
     per = max(1, int(round(0.5 / (DIAG_EVERY * dt))))
-    out = {"n": n, "steps": steps, "dt": dt, "t_end": steps * dt, "reference": "fp64 GPU",
-           "reference_seconds": el_ref, "modes": {}}
-    cases = [(m, None) for m in SWEEP if m != "fp64"] + [("fp16_fp32", "plain")]
+    at = lambda a: a[per - 1::per]       # -dK/dt samples at t = 0.5, 1, ... (index shift 1)
+    out = {"workload": args.accuracy_workload, "n": n, "steps": steps, "dt": dt,
+           "t_end": steps * dt, "reference": "fp64 GPU", "reference_seconds": el_ref,
+           "modes": {}}
+    # the FP64-compute mode costs a second FP64 run; the paper's TGSym study has no such mode
+    skip = ("fp64", "fp32s_fp64c") if sym else ("fp64",)
+    cases = [(m, None) for m in SWEEP if m not in skip] + [("fp16_fp32", "plain")]
     for mode, enc in cases:
         q, K, E, el = run(mode, enc)
         nrm = lambda a: float(torch.linalg.vector_norm(a))
@@ -129,6 +144,12 @@ def accuracy_sweep(args):
             "epsS": max(abs(a - b) for a, b in zip(E, E_ref)) / max(abs(b) for b in E_ref),
             "epsS_mean_abs_at_0.5": (sum(abs(E[i] - E_ref[i]) for i in range(0, nrec, per))
                                      / sum(abs(E_ref[i]) for i in range(0, nrec, per))),
+            "epsS_mean_abs_diff_at_0.5": (sum(abs(E[i] - E_ref[i]) for i in range(0, nrec, per))
+                                          / len(range(0, nrec, per))),
+            "dKdt_mean_abs_diff_at_0.5": (sum(abs(a - b) for a, b in zip(at(diss(K)), at(d_ref)))
+                                          / max(1, len(at(d_ref)))),
+            "dKdt_mean_abs_at_0.5": (sum(abs(a - b) for a, b in zip(at(diss(K)), at(d_ref)))
+                                     / max(1e-300, sum(abs(b) for b in at(d_ref)))),
             "seconds": el,
         }
         out["modes"][mode + ("" if enc is None else f"[{enc}]")] = rec
@@ -450,7 +471,7 @@ def extra_workloads(args, tgv, torch, dev, stream, peaks):
     # the paper's own workload: TGSym 256^3 (pi^3 box with mirror planes),
     # M = 0.5, Re = 800, dt = 0.0025; ms per iteration (one RK3 step) per mode,
     # beside the paper's A100 Storesome times (context, other hardware)
-    paper_ms = {"fp64": 50.31, "spdp": 37.60, "fp32": 25.00, "fp16": 18.67}
+    paper_ms = {"fp64": 50.31, "spdp": 37.60, "fp32": 25.00, "hpsp": 22.13, "fp16": 18.67}
     tgs = {}
     for mode in ("fp64", "spdp", "fp32", "hpsp", "fp16_fp32", "fp16"):
         cfg = tgv.Config(n=256, mode=mode, length=math.pi, symmetric=True, mach=0.5, re=800.0,
