@@ -25,9 +25,10 @@
 // over `zchunk` planes; each thread owns NP consecutive x points (a "unit";
 // NP = 2 pairs the FP32 arithmetic into f32x2 instructions and the shared
 // loads into 64-bit accesses).  Each z plane of the tile plus a 2-point halo
-// is read once from HBM (periodic wrap; the next plane is prefetched into
-// registers while the current one is computed), converted to the compute
-// type, and turned into primitives in a 6-plane shared-memory ring.  Per
+// is read once from HBM (periodic wrap, or mirror images in the symmetric
+// box; the next plane is staged into shared memory by cp.async while the
+// current one is computed), converted to the compute type, and turned into
+// primitives in a 6-plane shared-memory ring.  Per
 // plane, with two CTA barriers:
 //   1. primitives of the prefetched plane zl -> ring slot            | barrier
 //   2. prefetch plane zl+1; D_x u + D_y v of plane zl (z-taps of s_z);
@@ -264,7 +265,6 @@ __device__ __forceinline__ void stage_tile(const Problem& P, const StageArgs& S,
     for (int c = 0; c < 5; ++c)
       cp_async<sizeof(RawT)>(dst + c * NT + tid, qt + (long long)kq * nn + tile_off + c * n3);
   };
-  RawS qin_q[3][5];  // raw Q of the own unit at planes zl, zl-1, zl-2
   auto commit = [&](int slot, int zl) {  // staged raw plane -> primitives in the ring
     TC* base = ring + slot * NFLD * PL;
     bool fz;
@@ -276,14 +276,6 @@ __device__ __forceinline__ void stage_tile(const Problem& P, const StageArgs& S,
         RawS raw[5];
 #pragma unroll
         for (int c = 0; c < 5; ++c) raw[c] = stage_q[c * PLU + q];
-        if (r == 0) {
-#pragma unroll
-          for (int c = 0; c < 5; ++c) {
-            qin_q[2][c] = qin_q[1][c];
-            qin_q[1][c] = qin_q[0][c];
-            qin_q[0][c] = raw[c];
-          }
-        }
         const int e = eoff[r];
         V rho = IO::conv(raw[0]) + c_rho0;
         V ru = IO::conv(raw[1]), rv = IO::conv(raw[2]), rw = IO::conv(raw[3]);
@@ -498,6 +490,15 @@ __device__ __forceinline__ void stage_tile(const Problem& P, const StageArgs& S,
     // ---- phase B: x- and y-direction terms of the own unit, assembly, epilogue
     if (k >= z0 && active_xy) {
       const TC* P0 = pk[2];
+      // the epilogue's Q_in of the own unit at plane k, in storage precision
+      // (read two planes ago through the staging buffer, so a cache hit;
+      // issued here so that its latency hides behind the x/y terms)
+      RawS qin_raw[5];
+      if constexpr (EPI == EPI_RK) {
+#pragma unroll
+        for (int c = 0; c < 5; ++c)
+          qin_raw[c] = IO::load(q_in + (long long)k * nn + tile_off + c * n3);
+      }
 #pragma unroll
       for (int j = 0; j < 2; ++j) {
         auto tap = [&](int fld) -> Taps<V> {
@@ -607,13 +608,12 @@ __device__ __forceinline__ void stage_tile(const Problem& P, const StageArgs& S,
         TS* q_out = static_cast<TS*>(S.q_out);
         TT* qt = static_cast<TT*>(S.qt);
         const TA a = cvt<TA>(S.a), b = cvt<TA>(S.b), dt = cvt<TA>(S.dt);
-#pragma unroll
         if (S.read_qt) cp_async_wait<1>();  // this plane's Qt group has landed
         const RawT* qts = stage_t + (k & 1) * 5 * NT;
 #pragma unroll
         for (int c = 0; c < 5; ++c) {
           TA qtn[NP], qo[NP], qin[NP], qold[NP];
-          raw_elems<TA, NP>(qin_q[2][c], qin);
+          raw_elems<TA, NP>(qin_raw[c], qin);
           if (S.read_qt) raw_elems<TA, NP>(qts[c * NT + tid], qold);
 #pragma unroll
           for (int e = 0; e < NP; ++e) {
