@@ -55,6 +55,8 @@ def parse():
                          "the FP64 GPU path; prints one JSON object")
     ap.add_argument("--accuracy-steps", type=int, default=None,
                     help="default: 2000 (tgv), 8000 = t 20 (tgsym)")
+    ap.add_argument("--accuracy-modes", default=None,
+                    help="comma-separated subset of the sweep's modes (default: all)")
     ap.add_argument("--accuracy-workload", default="tgv", choices=["tgv", "tgsym"],
                     help="tgv: periodic 2 pi box, M 0.1, Re 1600, dt 0.00125 at 256^3; tgsym: "
                          "the symmetric pi box of Sec. 4.1/4.3, M 0.5, Re 800, dt 0.0025")
@@ -133,6 +135,9 @@ def accuracy_sweep(args):
     # the FP64-compute mode costs a second FP64 run; the paper's TGSym study has no such mode
     skip = ("fp64", "fp32s_fp64c") if sym else ("fp64",)
     cases = [(m, None) for m in SWEEP if m not in skip] + [("fp16_fp32", "plain")]
+    if args.accuracy_modes:
+        keep = set(args.accuracy_modes.split(","))
+        cases = [(m, e) for m, e in cases if m in keep]
     for mode, enc in cases:
         q, K, E, el = run(mode, enc)
         nrm = lambda a: float(torch.linalg.vector_norm(a))

@@ -95,15 +95,21 @@ static int32_t check(const tgv_config* c) {
 static int pick_tile(const tgv_config& c) {
   const ModeLaunchers& L = mode_launchers(find_mode(c));
   if (c.tile > 0) return L.smem[c.tile - 1] <= STAGE_SMEM_LIMIT ? c.tile - 1 : -1;
-  int best = -1;
-  long long best_area = -1;
+  // the first tile (the mode's own first choice, then the table order) whose
+  // padded plane is within 4% of the smallest padded plane of the tiles that fit
+  long long area[NUM_TILES], min_area = -1;
   for (int t = 0; t < NUM_TILES; ++t) {
-    if (L.smem[t] > STAGE_SMEM_LIMIT) continue;
     const int tx = tile_tx(c.compute, t), ty = tile_ty(c.compute, t);
-    const long long area = (long long)((c.n + tx - 1) / tx) * tx * ((c.n + ty - 1) / ty) * ty;
-    if (best_area < 0 || area < best_area) { best_area = area; best = t; }
+    area[t] = L.smem[t] > STAGE_SMEM_LIMIT
+                  ? -1
+                  : (long long)((c.n + tx - 1) / tx) * tx * ((c.n + ty - 1) / ty) * ty;
+    if (area[t] > 0 && (min_area < 0 || area[t] < min_area)) min_area = area[t];
   }
-  return best;
+  for (int i = -1; i < NUM_TILES; ++i) {
+    const int t = i < 0 ? L.first_tile : i;
+    if (area[t] > 0 && area[t] * 25 <= min_area * 26) return t;
+  }
+  return -1;
 }
 
 // Upper bound on the z chunks of one stage launch (bounds the CTA count, and

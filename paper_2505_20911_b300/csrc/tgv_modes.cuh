@@ -27,15 +27,16 @@ constexpr ModeKey MODE_KEYS[NUM_MODES] = {
 };
 
 // Tile shapes (TX, TY) and points per thread; tile id t is 1-based in the C
-// ABI.  FP32/FP16 compute uses two x points per thread; FP64 compute one, on
-// smaller tiles (an FP64 ring of a 32x16 tile would not fit shared memory).
-// A tile whose shared memory exceeds STAGE_SMEM_LIMIT for a mode's storage
-// types is not used for that mode.
+// ABI, in order of preference (larger tiles carry less halo).  FP32/FP16
+// compute uses two x points per thread; FP64 compute one, on smaller tiles
+// (an FP64 ring of a 32x16 tile would not fit shared memory).  A tile whose
+// shared memory exceeds STAGE_SMEM_LIMIT for a mode's storage types is not
+// used for that mode.
 constexpr int NUM_TILES = 3;
 constexpr int TILE_TX[NUM_TILES] = {32, 16, 16};
 constexpr int TILE_TY[NUM_TILES] = {16, 16, 8};
 constexpr int TILE_TX_F64[NUM_TILES] = {16, 16, 8};
-constexpr int TILE_TY_F64[NUM_TILES] = {8, 8, 8};
+constexpr int TILE_TY_F64[NUM_TILES] = {16, 8, 8};
 
 inline int tile_tx(int comp, int t) { return comp == TGV_F64 ? TILE_TX_F64[t] : TILE_TX[t]; }
 inline int tile_ty(int comp, int t) { return comp == TGV_F64 ? TILE_TY_F64[t] : TILE_TY[t]; }
@@ -53,6 +54,7 @@ struct ModeLaunchers {
   StageFn stage_kgp[NUM_TILES], stage_kgp_diag[NUM_TILES], rhs_kgp[NUM_TILES];
   OccFn occupancy[NUM_TILES];    // resident CTAs per SM of the EPI_RK kernel
   size_t smem[NUM_TILES];        // dynamic shared memory per CTA
+  int first_tile = 0;            // tile tried before the table order
   InitFn init;
   DiagFn diag_partial;
 };

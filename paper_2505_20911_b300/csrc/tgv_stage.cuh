@@ -28,7 +28,7 @@
 // is read once from HBM (periodic wrap, or mirror images in the symmetric
 // box; the next plane is staged into shared memory by cp.async while the
 // current one is computed), converted to the compute type, and turned into
-// primitives in a 6-plane shared-memory ring.  Per
+// primitives in a 5-plane shared-memory ring.  Per
 // plane, with two CTA barriers:
 //   1. primitives of the prefetched plane zl -> ring slot            | barrier
 //   2. prefetch plane zl+1; D_x u + D_y v of plane zl (z-taps of s_z);
@@ -56,13 +56,18 @@ struct StageArgs {
   int zchunk;         // z planes per CTA
 };
 
-// Ring-plane fields (compute type).
-enum { F_RHO = 0, F_RU, F_RV, F_RW, F_RE, F_U, F_V, F_W, F_P, F_H0, NFLD };
+// Ring-plane fields (compute type).  rho w is not kept: its taps are formed
+// as rho * w (one multiply per tap instead of one shared-memory load).
+enum { F_RHO = 0, F_RU, F_RV, F_RE, F_U, F_V, F_W, F_P, F_H0, NFLD };
+// Ring field of conserved component c (rho w: none).
+__host__ __device__ constexpr int cons_field(int c) { return c < 3 ? c : (c == 4 ? F_RE : -1); }
 // Strip fields of the centre plane.
 enum { S_SX = 0, S_SY, S_GX, S_GY, NSTRIP };
-// Ring depth: planes k-2..k+2 are read while the next plane is committed
-// before the first barrier, so the primitives ring needs 6 slots.
-constexpr int NSLOT = 6;
+// Ring depth: phase A of centre plane k reads planes k-2..k+2; phase B reads
+// only plane k and the strips, so the commit of plane k+3 (which follows the
+// phase-B of plane k-1 and precedes the first barrier) may overwrite plane
+// k-3's slot: 5 slots.
+constexpr int NSLOT = 5;
 
 template <int TX, int TY, int NP>
 struct Geo {
@@ -299,7 +304,6 @@ __device__ __forceinline__ void stage_tile(const Problem& P, const StageArgs& S,
         rho.store(base + F_RHO * PL + e);
         ru.store(base + F_RU * PL + e);
         rv.store(base + F_RV * PL + e);
-        rw.store(base + F_RW * PL + e);
         rE.store(base + F_RE * PL + e);
         uu.store(base + F_U * PL + e);
         vv.store(base + F_V * PL + e);
@@ -389,13 +393,15 @@ __device__ __forceinline__ void stage_tile(const Problem& P, const StageArgs& S,
       };
       // own unit (tile point)
       {
-#pragma unroll
-        for (int c = 0; c < 5; ++c) fc[c] = V::load(P0 + c * PL + ec);
         h0c = V::load(P0 + F_H0 * PL + ec);
         const Taps<V> ux = xt(P0 + F_U * PL, ec, uc[0]);
         const Taps<V> uy = yt(P0 + F_U * PL, ec), vy = yt(P0 + F_V * PL, ec);
         uc[1] = V::load(P0 + F_V * PL + ec);
         uc[2] = V::load(P0 + F_W * PL + ec);
+#pragma unroll
+        for (int c = 0; c < 5; ++c)
+          if (c != 3) fc[c] = V::load(P0 + cons_field(c) * PL + ec);
+        fc[3] = fc[0] * uc[2];
         const Taps<V> uz = ztw(F_U, ec), vz = ztw(F_V, ec), wz = ztw(F_W, ec);
         const V dxu = c_inv12h * dsum(ux, c_8);
         const V dyv = c_inv12h * dsum(vy, c_8);
@@ -417,11 +423,11 @@ __device__ __forceinline__ void stage_tile(const Problem& P, const StageArgs& S,
         Taps<V> F0z, F4z;
 #pragma unroll
         for (int c = 0; c < 5; ++c) {
-          const Taps<V> F = ztw(c, ec);
+          const Taps<V> F = c == 3 ? tmul(F0z, U) : ztw(cons_field(c), ec);
           const V dF = dsum(F, c_8);
           dFz[c] = dF;
+          if (c == 0) F0z = F;
           if constexpr (KGP) {
-            if (c == 0) F0z = F;
             if (c == 4) F4z = F;
           }
           udf[c] = fma(uc[2], dF, udf[c]);
@@ -508,16 +514,17 @@ __device__ __forceinline__ void stage_tile(const Problem& P, const StageArgs& S,
         const Taps<V> U = tap(F_U + j);
         const Taps<V> aU = tscale(c_alpha, U);
         const Taps<V> Pt = tap(F_P);
+        const Taps<V> Wt = tap(F_W);
         V dFj[5];
         Taps<V> F0j, F4j;
         // conserved components: D_j f_c, a D_j(u_j f_c) with merged pressure
 #pragma unroll
         for (int c = 0; c < 5; ++c) {
-          const Taps<V> F = tap(c);
+          const Taps<V> F = c == 3 ? tmul(F0j, Wt) : tap(cons_field(c));
           const V dF = dsum(F, c_8);
           dFj[c] = dF;
+          if (c == 0) F0j = F;
           if constexpr (KGP) {
-            if (c == 0) F0j = F;
             if (c == 4) F4j = F;
           }
           udf[c] = fma(uc[j], dF, udf[c]);
@@ -531,7 +538,7 @@ __device__ __forceinline__ void stage_tile(const Problem& P, const StageArgs& S,
         }
         Taps<V> Uall[3];
 #pragma unroll
-        for (int i = 0; i < 3; ++i) Uall[i] = (i == j) ? U : tap(F_U + i);
+        for (int i = 0; i < 3; ++i) Uall[i] = (i == j) ? U : (i == 2 ? Wt : tap(F_U + i));
         if constexpr (KGP) kgp_extra(j, U, Uall, F0j, F4j, dFj, fc, uc, c_8, kx);
         // velocity second derivatives (and first derivatives for diagnostics)
 #pragma unroll
