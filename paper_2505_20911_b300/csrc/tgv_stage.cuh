@@ -270,6 +270,19 @@ __device__ __forceinline__ void stage_tile(const Problem& P, const StageArgs& S,
     for (int c = 0; c < 5; ++c)
       cp_async<sizeof(RawT)>(dst + c * NT + tid, qt + (long long)kq * nn + tile_off + c * n3);
   };
+  // The epilogue's Q_in of the own unit, in storage precision: with FP32
+  // compute and storage of at most 32 bits it is carried from the plane
+  // loader in a three-plane register queue (planes zl, zl-1, zl-2; zeroed
+  // first, so no entry is read before it is written), otherwise re-read at the
+  // start of phase B (a cache hit: the loader read it two planes earlier).
+  // Measured at 256^3: the queue is 3-4% faster in the FP32-compute modes,
+  // the re-read 15% faster in pure half.
+  constexpr bool QIN_QUEUE = std::is_same<TC, float>::value && sizeof(TS) <= 4;
+  RawS qin_q[QIN_QUEUE ? 3 : 1][5];
+#pragma unroll
+  for (int d = 0; d < (QIN_QUEUE ? 3 : 1); ++d)
+#pragma unroll
+    for (int c = 0; c < 5; ++c) qin_q[d][c] = RawS{};
   auto commit = [&](int slot, int zl) {  // staged raw plane -> primitives in the ring
     TC* base = ring + slot * NFLD * PL;
     bool fz;
@@ -281,6 +294,16 @@ __device__ __forceinline__ void stage_tile(const Problem& P, const StageArgs& S,
         RawS raw[5];
 #pragma unroll
         for (int c = 0; c < 5; ++c) raw[c] = stage_q[c * PLU + q];
+        if constexpr (QIN_QUEUE) {
+          if (r == 0) {
+#pragma unroll
+            for (int c = 0; c < 5; ++c) {
+              qin_q[2][c] = qin_q[1][c];
+              qin_q[1][c] = qin_q[0][c];
+              qin_q[0][c] = raw[c];
+            }
+          }
+        }
         const int e = eoff[r];
         V rho = IO::conv(raw[0]) + c_rho0;
         V ru = IO::conv(raw[1]), rv = IO::conv(raw[2]), rw = IO::conv(raw[3]);
@@ -496,14 +519,12 @@ __device__ __forceinline__ void stage_tile(const Problem& P, const StageArgs& S,
     // ---- phase B: x- and y-direction terms of the own unit, assembly, epilogue
     if (k >= z0 && active_xy) {
       const TC* P0 = pk[2];
-      // the epilogue's Q_in of the own unit at plane k, in storage precision
-      // (read two planes ago through the staging buffer, so a cache hit;
-      // issued here so that its latency hides behind the x/y terms)
-      RawS qin_raw[5];
-      if constexpr (EPI == EPI_RK) {
+      // the epilogue's Q_in of the own unit at plane k (see QIN_QUEUE),
+      // issued here so that its latency hides behind the x/y terms
+      if constexpr (EPI == EPI_RK && !QIN_QUEUE) {
 #pragma unroll
         for (int c = 0; c < 5; ++c)
-          qin_raw[c] = IO::load(q_in + (long long)k * nn + tile_off + c * n3);
+          qin_q[0][c] = IO::load(q_in + (long long)k * nn + tile_off + c * n3);
       }
 #pragma unroll
       for (int j = 0; j < 2; ++j) {
@@ -620,7 +641,7 @@ __device__ __forceinline__ void stage_tile(const Problem& P, const StageArgs& S,
 #pragma unroll
         for (int c = 0; c < 5; ++c) {
           TA qtn[NP], qo[NP], qin[NP], qold[NP];
-          raw_elems<TA, NP>(qin_raw[c], qin);
+          raw_elems<TA, NP>(qin_q[QIN_QUEUE ? 2 : 0][c], qin);
           if (S.read_qt) raw_elems<TA, NP>(qts[c * NT + tid], qold);
 #pragma unroll
           for (int e = 0; e < NP; ++e) {
