@@ -404,6 +404,7 @@ __device__ __forceinline__ void stage_tile(const Problem& P, const StageArgs& S,
     V suf[5], udf[5], d2u[3], ds[3], kx[5];
     V d2h = zero, dus = zero;
     V grad[3][3];  // grad[i][j] = raw D_j u_i (diagnostics)
+    Taps<V> ux_c, uy_c, vy_c;  // x taps of u, y taps of u and v: phase A loads them, phase B reuses
 #pragma unroll
     for (int c = 0; c < 5; ++c) { suf[c] = zero; udf[c] = zero; fc[c] = zero; kx[c] = zero; }
 #pragma unroll
@@ -419,6 +420,9 @@ __device__ __forceinline__ void stage_tile(const Problem& P, const StageArgs& S,
         h0c = V::load(P0 + F_H0 * PL + ec);
         const Taps<V> ux = xt(P0 + F_U * PL, ec, uc[0]);
         const Taps<V> uy = yt(P0 + F_U * PL, ec), vy = yt(P0 + F_V * PL, ec);
+        ux_c = ux;
+        uy_c = uy;
+        vy_c = vy;
         uc[1] = V::load(P0 + F_V * PL + ec);
         uc[2] = V::load(P0 + F_W * PL + ec);
 #pragma unroll
@@ -532,7 +536,7 @@ __device__ __forceinline__ void stage_tile(const Problem& P, const StageArgs& S,
           if (j == 0) { V cd; return xt(P0 + fld * PL, ec, cd); }
           return yt(P0 + fld * PL, ec);
         };
-        const Taps<V> U = tap(F_U + j);
+        const Taps<V> U = j == 0 ? ux_c : vy_c;
         const Taps<V> aU = tscale(c_alpha, U);
         const Taps<V> Pt = tap(F_P);
         const Taps<V> Wt = tap(F_W);
@@ -559,7 +563,8 @@ __device__ __forceinline__ void stage_tile(const Problem& P, const StageArgs& S,
         }
         Taps<V> Uall[3];
 #pragma unroll
-        for (int i = 0; i < 3; ++i) Uall[i] = (i == j) ? U : (i == 2 ? Wt : tap(F_U + i));
+        for (int i = 0; i < 3; ++i)
+          Uall[i] = (i == j) ? U : (i == 2 ? Wt : ((j == 1 && i == 0) ? uy_c : tap(F_U + i)));
         if constexpr (KGP) kgp_extra(j, U, Uall, F0j, F4j, dFj, fc, uc, c_8, kx);
         // velocity second derivatives (and first derivatives for diagnostics)
 #pragma unroll
