@@ -39,6 +39,21 @@ used):
         C_phi = 1/4 sum_j [ D_j(rho u_j phi) + rho D_j(u_j phi) + u_j D_j(rho phi)
                 + phi D_j(rho u_j) + rho u_j D_j phi + rho phi D_j u_j
                 + u_j phi D_j rho ].
+  R14 KEEP (kinetic energy and entropy preserving) split of the same study,
+      which the paper cites without printing it.  Reading: the second-order
+      two-point fluxes of Kuya, Totani and Kawai (2018),
+        mass rho_bar u_bar,  momentum rho_bar u_bar (u_i)_bar + p_bar,
+        energy rho_bar u_bar e_bar + rho_bar u_bar (u_i u_i)~/2 + (p u)~,
+      (bar: mean of the two points; (a b)~ = (a_l b_r + a_r b_l)/2), carried
+      to the 4th-order stencil by the two-point-flux form of central
+      differences (a flux difference with weights 2 a_l over the point pairs
+      l apart).  The equivalent split form, which this code evaluates: mass
+      and momentum as the KGP split above; energy as the KGP split of the
+      internal energy (phi = e, rho phi = p/(gamma-1)) plus
+        1/4 sum_j sum_c [ rho u_j v_c D_j v_c + v_c D_j(rho u_j v_c)
+                          + rho v_c D_j(u_j v_c) + u_j v_c D_j(rho v_c) ]
+      for the kinetic energy, and the pressure work as
+        sum_j [ u_j D_j p + p D_j u_j ].
   R4  Viscous terms, all in conservative (telescoping) form so that mass,
       momentum and total energy are conserved to round-off on the periodic box:
         momentum i: (mu/Re)[ sum_j D2_j u_i + 1/3 D2_i u_i + 1/3 D_i s_i ],
@@ -90,7 +105,7 @@ class Flow:
     re: float = 1600.0
     pr: float = 0.71
     mu: float = 1.0
-    split: str = "blaisdell"  # "divergence" (the foil of Sec. 4.2) or "kgp" (cubic)
+    split: str = "blaisdell"  # "divergence" (the foil of Sec. 4.2), "kgp" or "keep" (cubic)
     length: float = 2.0 * math.pi
     offset: float = 0.0       # grid points at (i + offset) h; 0.5 = cell-centred
     symmetric: bool = False   # symmetry planes on every face (reading R13)
@@ -177,13 +192,17 @@ def convective(flow: Flow, q: torch.Tensor) -> torch.Tensor:
         C_phi = 1/2 sum_j [ D_j(u_j (rho phi)) + u_j D_j(rho phi) + (rho phi) D_j u_j ],
     using rho u_j phi = u_j (rho phi); (rho phi) are the components of Q.
     Divergence form: C_phi = sum_j D_j(u_j (rho phi)).  KGP cubic form: the
-    seven-term quarter average of reading R3."""
+    seven-term quarter average of reading R3.  KEEP (reading R14): KGP for
+    phi = 1 and u_i; for the energy, KGP of the internal energy plus the
+    kinetic-energy split (its pressure work is in ``pressure_terms``)."""
     h = flow.h
     rho = q[0]
     vel = (q[1] / rho, q[2] / rho, q[3] / rho)
     out = []
     for c in range(5):
         f = q[c]  # rho * phi
+        if flow.split == "keep" and c == 4:
+            f = primitives(flow, q)[4] / (flow.gamma - 1.0)  # rho e
         phi = f / rho
         acc = torch.zeros_like(f)
         for j in range(3):
@@ -192,11 +211,17 @@ def convective(flow: Flow, q: torch.Tensor) -> torch.Tensor:
                 acc = acc + flux
             elif flow.split == "blaisdell":
                 acc = acc + 0.5 * (flux + vel[j] * d1(f, j, h) + f * d1(vel[j], j, h))
-            elif flow.split == "kgp":
+            elif flow.split in ("kgp", "keep"):
                 m_j = q[1 + j]  # rho u_j
                 acc = acc + 0.25 * (flux + rho * d1(vel[j] * phi, j, h) + vel[j] * d1(f, j, h)
                                     + phi * d1(m_j, j, h) + m_j * d1(phi, j, h)
                                     + f * d1(vel[j], j, h) + vel[j] * phi * d1(rho, j, h))
+                if flow.split == "keep" and c == 4:
+                    for cc in range(3):  # kinetic energy: v_c = velocity component cc
+                        v = vel[cc]
+                        acc = acc + 0.25 * (m_j * v * d1(v, j, h) + v * d1(m_j * v, j, h)
+                                            + rho * v * d1(vel[j] * v, j, h)
+                                            + vel[j] * v * d1(rho * v, j, h))
             else:
                 raise ValueError(f"unknown split form {flow.split!r}")
         out.append(acc)
@@ -205,12 +230,16 @@ def convective(flow: Flow, q: torch.Tensor) -> torch.Tensor:
 
 def pressure_terms(flow: Flow, q: torch.Tensor) -> torch.Tensor:
     """Pressure gradient (momentum) and pressure work (energy), divergence form:
-    (0, D_x p, D_y p, D_z p, sum_j D_j(p u_j))."""
+    (0, D_x p, D_y p, D_z p, sum_j D_j(p u_j)); with KEEP (reading R14) the
+    work is split as sum_j (u_j D_j p + p D_j u_j)."""
     h = flow.h
     rho, u, v, w, p, _ = primitives(flow, q)
     vel = (u, v, w)
     zero = torch.zeros_like(rho)
-    work = sum(d1(p * vel[j], j, h) for j in range(3))
+    if flow.split == "keep":
+        work = sum(vel[j] * d1(p, j, h) + p * d1(vel[j], j, h) for j in range(3))
+    else:
+        work = sum(d1(p * vel[j], j, h) for j in range(3))
     return torch.stack([zero, d1(p, 0, h), d1(p, 1, h), d1(p, 2, h), work])
 
 

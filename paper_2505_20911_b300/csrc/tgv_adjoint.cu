@@ -291,7 +291,8 @@ static bool adjoint_mode_ok(const tgv_config& c) {
                    c.accumulate == TGV_F64;
   const bool f32 = c.q_storage == TGV_F32 && c.qt_storage == TGV_F32 && c.compute == TGV_F32 &&
                    c.accumulate == TGV_F32;
-  return (f64 || f32) && c.encoding == TGV_ENC_PLAIN && c.split_form != TGV_SPLIT_KGP &&
+  return (f64 || f32) && c.encoding == TGV_ENC_PLAIN &&
+         (c.split_form == TGV_SPLIT_BLAISDELL || c.split_form == TGV_SPLIT_DIVERGENCE) &&
          !(c.flags & TGV_FLAG_SYMMETRIC);
 }
 

@@ -74,7 +74,7 @@ static int32_t check(const tgv_config* c) {
   if (!c) return TGV_ERR_ARG;
   if (c->n < 8 || c->n > 1024 || (c->n & 1)) return TGV_ERR_ARG;
   if (c->split_form != TGV_SPLIT_BLAISDELL && c->split_form != TGV_SPLIT_DIVERGENCE &&
-      c->split_form != TGV_SPLIT_KGP)
+      c->split_form != TGV_SPLIT_KGP && c->split_form != TGV_SPLIT_KEEP)
     return TGV_ERR_ARG;
   if (!valid_dtype(c->q_storage) || !valid_dtype(c->qt_storage) || !valid_dtype(c->compute) ||
       !valid_dtype(c->accumulate))
@@ -262,6 +262,8 @@ static int32_t launch_stage_common(const tgv_config* cfg, const StageArgs& S, bo
   StageFn fn;
   if (cfg->split_form == TGV_SPLIT_KGP)
     fn = rhs ? L.rhs_kgp[tile] : (S.diag_part ? L.stage_kgp_diag[tile] : L.stage_kgp[tile]);
+  else if (cfg->split_form == TGV_SPLIT_KEEP)
+    fn = rhs ? L.rhs_keep[tile] : (S.diag_part ? L.stage_keep_diag[tile] : L.stage_keep[tile]);
   else
     fn = rhs ? L.rhs[tile] : (S.diag_part ? L.stage_diag[tile] : L.stage[tile]);
   if (!fn) return TGV_ERR_UNSUPPORTED;

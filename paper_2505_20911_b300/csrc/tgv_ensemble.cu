@@ -160,7 +160,8 @@ static int32_t ens_check(const tgv_config* cfgs, int32_t count, void* const* q_a
     if (!(c.q_storage == TGV_F32 && c.qt_storage == TGV_F32 && c.compute == TGV_F32 &&
           c.accumulate == TGV_F32))
       return TGV_ERR_UNSUPPORTED;
-    if (c.split_form == TGV_SPLIT_KGP) return TGV_ERR_UNSUPPORTED;
+    if (c.split_form != TGV_SPLIT_BLAISDELL && c.split_form != TGV_SPLIT_DIVERGENCE)
+      return TGV_ERR_UNSUPPORTED;
     if (!q_a[i] || !q_b[i] || !qt[i] || q_a[i] == q_b[i]) return TGV_ERR_ARG;
     if (!std::isfinite(dts[i]) || !(dts[i] > 0.0)) return TGV_ERR_ARG;
     if (!(c.flags & TGV_FLAG_ALLOW_UNSTABLE_DT) && dts[i] > tgv_dt_max(&c)) return TGV_ERR_UNSTABLE_DT;

@@ -50,8 +50,9 @@ struct ModeLaunchers {
   StageFn stage[NUM_TILES];      // EPI_RK
   StageFn stage_diag[NUM_TILES]; // EPI_RK with the fused diagnostics of its input
   StageFn rhs[NUM_TILES];        // EPI_RHS
-  // the cubic KGP split (null where a mode does not build it)
+  // the cubic KGP and KEEP splits (null where a mode does not build them)
   StageFn stage_kgp[NUM_TILES], stage_kgp_diag[NUM_TILES], rhs_kgp[NUM_TILES];
+  StageFn stage_keep[NUM_TILES], stage_keep_diag[NUM_TILES], rhs_keep[NUM_TILES];
   OccFn occupancy[NUM_TILES];    // resident CTAs per SM of the EPI_RK kernel
   size_t smem[NUM_TILES];        // dynamic shared memory per CTA
   int first_tile = 0;            // tile tried before the table order
@@ -62,9 +63,9 @@ struct ModeLaunchers {
 const ModeLaunchers& mode_launchers(int mode);
 
 template <class TS, class TT, class TC, class TA, int TX, int TY, int NP, int EPI, bool DIAG,
-          bool KGP = false>
+          int SPL = SPL_QUAD>
 cudaError_t launch_stage(const Problem& P, const StageArgs& S, int zchunk, cudaStream_t st) {
-  auto kern = stage_kernel<TS, TT, TC, TA, TX, TY, NP, EPI, DIAG, KGP>;
+  auto kern = stage_kernel<TS, TT, TC, TA, TX, TY, NP, EPI, DIAG, SPL>;
   const size_t smem = stage_smem_bytes<TS, TT, TC, TX, TY, NP>();
   if (smem > STAGE_SMEM_LIMIT) return cudaErrorInvalidConfiguration;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -113,18 +114,22 @@ void set_tile(ModeLaunchers& L, int t) {
   L.stage_diag[t] = launch_stage<TS, TT, TC, TA, TX, TY, NP, EPI_RK, true>;
   L.rhs[t] = launch_stage<TS, TT, TC, TA, TX, TY, NP, EPI_RHS, false>;
   if constexpr (WITH_KGP) {
-    L.stage_kgp[t] = launch_stage<TS, TT, TC, TA, TX, TY, NP, EPI_RK, false, true>;
-    L.stage_kgp_diag[t] = launch_stage<TS, TT, TC, TA, TX, TY, NP, EPI_RK, true, true>;
-    L.rhs_kgp[t] = launch_stage<TS, TT, TC, TA, TX, TY, NP, EPI_RHS, false, true>;
+    L.stage_kgp[t] = launch_stage<TS, TT, TC, TA, TX, TY, NP, EPI_RK, false, SPL_KGP>;
+    L.stage_kgp_diag[t] = launch_stage<TS, TT, TC, TA, TX, TY, NP, EPI_RK, true, SPL_KGP>;
+    L.rhs_kgp[t] = launch_stage<TS, TT, TC, TA, TX, TY, NP, EPI_RHS, false, SPL_KGP>;
+    L.stage_keep[t] = launch_stage<TS, TT, TC, TA, TX, TY, NP, EPI_RK, false, SPL_KEEP>;
+    L.stage_keep_diag[t] = launch_stage<TS, TT, TC, TA, TX, TY, NP, EPI_RK, true, SPL_KEEP>;
+    L.rhs_keep[t] = launch_stage<TS, TT, TC, TA, TX, TY, NP, EPI_RHS, false, SPL_KEEP>;
   } else {
     L.stage_kgp[t] = L.stage_kgp_diag[t] = L.rhs_kgp[t] = nullptr;
+    L.stage_keep[t] = L.stage_keep_diag[t] = L.rhs_keep[t] = nullptr;
   }
   L.occupancy[t] = stage_occupancy<TS, TT, TC, TA, TX, TY, NP>;
   L.smem[t] = stage_smem_bytes<TS, TT, TC, TX, TY, NP>();
 }
 
-// WITH_KGP: also build the cubic KGP split (the FP64, FP32 and Q FP32 / Qt
-// FP16 modes: the precisions of the paper's split-form study).
+// WITH_KGP: also build the cubic KGP and KEEP splits (the FP64, FP32 and
+// Q FP32 / Qt FP16 modes: the precisions of the paper's split-form study).
 template <class TS, class TT, class TC, class TA, bool WITH_KGP = false>
 ModeLaunchers make_launchers() {
   ModeLaunchers L;

@@ -43,6 +43,12 @@
 namespace tgv {
 
 enum { EPI_RK = 0, EPI_RHS = 1 };
+// Convective split families built as kernel variants: the quadratic forms
+// (Blaisdell, divergence: runtime coefficients), the cubic KGP split, and KEEP
+// (KGP for mass and momentum, the kinetic-energy and entropy preserving
+// energy split of the two-point fluxes rho_bar u_bar e_bar
+// + rho_bar u_bar (u_i u_i)~/2 + (p u)~).
+enum { SPL_QUAD = 0, SPL_KGP = 1, SPL_KEEP = 2 };
 
 struct StageArgs {
   const void* q_in;   // Q layout, storage type TS
@@ -165,8 +171,31 @@ __device__ __forceinline__ void kgp_extra(const int j, const Taps<V>& U, const T
   }
 }
 
+// KEEP energy terms of direction j beyond the KGP split of the internal
+// energy, as raw sums added to kx[4] (which the assembly scales by 1/4 and
+// 1/12h): the kinetic-energy split
+//   sum_c [ m_j v_c D v_c + v_c D(u_j rho v_c) + rho v_c D(u_j v_c) + u_j v_c D(rho v_c) ]
+// and four times the pressure work u_j D p + p D u_j.  Fm: taps of rho v_c.
+template <class V>
+__device__ __forceinline__ void keep_extra(const int j, const Taps<V>& U, const Taps<V>* Ui,
+                                           const Taps<V>* Fm, const Taps<V>& Pt, const V* dF,
+                                           const V* fc, const V* uc, const V& pc, const V& c8,
+                                           const V& c4, V* kx) {
+  const V mj = fc[1 + j];
+  V acc = c4 * fma(uc[j], dsum(Pt, c8), pc * dsum(U, c8));
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    const V vc = uc[c];
+    acc = fma(mj * vc, dsum(Ui[c], c8), acc);
+    acc = fma(vc, dsum(tmul(U, Fm[c]), c8), acc);
+    acc = fma(fc[1 + c], dsum(tmul(U, Ui[c]), c8), acc);
+    acc = fma(uc[j] * vc, dF[1 + c], acc);
+  }
+  kx[4] = kx[4] + acc;
+}
+
 template <class TS, class TT, class TC, class TA, int TX, int TY, int NP, int EPI, bool DIAG,
-          bool KGP = false>
+          int SPL = SPL_QUAD>
 __device__ __forceinline__ void stage_tile(const Problem& P, const StageArgs& S, const int x0,
                                            const int y0, const int z0, const long long cta) {
   using G = Geo<TX, TY, NP>;
@@ -197,8 +226,10 @@ __device__ __forceinline__ void stage_tile(const Problem& P, const StageArgs& S,
   const V c_m53 = V::splat(cvt<TC>(-5.0 / 3.0)), c_one = V::splat(cvt<TC>(1.0));
   // convective split: a sum_j D_j(u_j f) + b (sum_j u_j D_j f + f div u) [+ b kx]
   const bool blaisdell = (P.split == TGV_SPLIT_BLAISDELL);
-  const V c_alpha = V::splat(cvt<TC>(KGP ? 0.25 : (blaisdell ? 0.5 : 1.0)));
-  const V c_beta = V::splat(cvt<TC>(KGP ? 0.25 : (blaisdell ? 0.5 : 0.0)));
+  constexpr bool CUBIC = SPL != SPL_QUAD, KEEP = SPL == SPL_KEEP;
+  const V c_alpha = V::splat(cvt<TC>(CUBIC ? 0.25 : (blaisdell ? 0.5 : 1.0)));
+  const V c_beta = V::splat(cvt<TC>(CUBIC ? 0.25 : (blaisdell ? 0.5 : 0.0)));
+  const V c_ig1 = V::splat(cvt<TC>(1.0 / P.gm1)), c_4 = V::splat(cvt<TC>(4.0));
 
   // ---- region units this thread loads and converts each plane.  Unit q < NT
   // is thread q's own tile unit; units q >= NT are the halo (rows 0-1, the
@@ -401,12 +432,16 @@ __device__ __forceinline__ void stage_tile(const Problem& P, const StageArgs& S,
     // shared with the strips).  The partial sums stay in registers across the
     // barrier and phase B adds the x and y directions.
     V fc[5], uc[3], h0c = zero, div = zero;
+    V fcc[5];     // rho phi of the convective split (KEEP: rho e in place of rho E)
+    V pc = zero;  // centre pressure (KEEP)
     V suf[5], udf[5], d2u[3], ds[3], kx[5];
     V d2h = zero, dus = zero;
     V grad[3][3];  // grad[i][j] = raw D_j u_i (diagnostics)
     Taps<V> ux_c, uy_c, vy_c;  // x taps of u, y taps of u and v: phase A loads them, phase B reuses
 #pragma unroll
-    for (int c = 0; c < 5; ++c) { suf[c] = zero; udf[c] = zero; fc[c] = zero; kx[c] = zero; }
+    for (int c = 0; c < 5; ++c) {
+      suf[c] = zero; udf[c] = zero; fc[c] = zero; kx[c] = zero; fcc[c] = zero;
+    }
 #pragma unroll
     for (int i = 0; i < 3; ++i) { d2u[i] = zero; ds[i] = zero; uc[i] = zero; }
     if (k >= z0) {
@@ -429,6 +464,12 @@ __device__ __forceinline__ void stage_tile(const Problem& P, const StageArgs& S,
         for (int c = 0; c < 5; ++c)
           if (c != 3) fc[c] = V::load(P0 + cons_field(c) * PL + ec);
         fc[3] = fc[0] * uc[2];
+#pragma unroll
+        for (int c = 0; c < 5; ++c) fcc[c] = fc[c];
+        if constexpr (KEEP) {
+          pc = V::load(P0 + F_P * PL + ec);
+          fcc[4] = c_ig1 * pc;
+        }
         const Taps<V> uz = ztw(F_U, ec), vz = ztw(F_V, ec), wz = ztw(F_W, ec);
         const V dxu = c_inv12h * dsum(ux, c_8);
         const V dyv = c_inv12h * dsum(vy, c_8);
@@ -447,28 +488,33 @@ __device__ __forceinline__ void stage_tile(const Problem& P, const StageArgs& S,
         const Taps<V> aU = tscale(c_alpha, U);
         const Taps<V> Pt = ztw(F_P, ec);
         V dFz[5];
-        Taps<V> F0z, F4z;
+        Taps<V> F0z, F4z, Fmz[3];
 #pragma unroll
         for (int c = 0; c < 5; ++c) {
-          const Taps<V> F = c == 3 ? tmul(F0z, U) : ztw(cons_field(c), ec);
+          const Taps<V> F = c == 3 ? tmul(F0z, U)
+                                   : ((KEEP && c == 4) ? tscale(c_ig1, Pt) : ztw(cons_field(c), ec));
           const V dF = dsum(F, c_8);
           dFz[c] = dF;
           if (c == 0) F0z = F;
-          if constexpr (KGP) {
+          if constexpr (CUBIC) {
             if (c == 4) F4z = F;
+          }
+          if constexpr (KEEP) {
+            if (c >= 1 && c <= 3) Fmz[c - 1] = F;
           }
           udf[c] = fma(uc[2], dF, udf[c]);
           if (c == 0) continue;
           Taps<V> g;
           if (c == 3) g = tfma(aU, F, Pt);                      // a w rho w + p
-          else if (c == 4) g = tmul(U, taxpy(c_alpha, F, Pt));  // w (a rho E + p)
+          else if (c == 4 && !KEEP) g = tmul(U, taxpy(c_alpha, F, Pt));  // w (a rho E + p)
           else g = tmul(aU, F);
           suf[c] = suf[c] + dsum(g, c_8);
           if (c == 3) suf[0] = fma(c_alpha, dF, suf[0]);  // D_z(rho w)
         }
-        if constexpr (KGP) {
+        if constexpr (CUBIC) {
           const Taps<V> UZall[3] = {uz, vz, wz};
-          kgp_extra(2, U, UZall, F0z, F4z, dFz, fc, uc, c_8, kx);
+          kgp_extra(2, U, UZall, F0z, F4z, dFz, fcc, uc, c_8, kx);
+          if constexpr (KEEP) keep_extra(2, U, UZall, Fmz, Pt, dFz, fc, uc, pc, c_8, c_4, kx);
         }
         const Taps<V>* UZ[3] = {&uz, &vz, &wz};
 #pragma unroll
@@ -541,22 +587,26 @@ __device__ __forceinline__ void stage_tile(const Problem& P, const StageArgs& S,
         const Taps<V> Pt = tap(F_P);
         const Taps<V> Wt = tap(F_W);
         V dFj[5];
-        Taps<V> F0j, F4j;
+        Taps<V> F0j, F4j, Fmj[3];
         // conserved components: D_j f_c, a D_j(u_j f_c) with merged pressure
 #pragma unroll
         for (int c = 0; c < 5; ++c) {
-          const Taps<V> F = c == 3 ? tmul(F0j, Wt) : tap(cons_field(c));
+          const Taps<V> F = c == 3 ? tmul(F0j, Wt)
+                                   : ((KEEP && c == 4) ? tscale(c_ig1, Pt) : tap(cons_field(c)));
           const V dF = dsum(F, c_8);
           dFj[c] = dF;
           if (c == 0) F0j = F;
-          if constexpr (KGP) {
+          if constexpr (CUBIC) {
             if (c == 4) F4j = F;
+          }
+          if constexpr (KEEP) {
+            if (c >= 1 && c <= 3) Fmj[c - 1] = F;
           }
           udf[c] = fma(uc[j], dF, udf[c]);
           if (c == 0) continue;
           Taps<V> g;
           if (c == 1 + j) g = tfma(aU, F, Pt);                 // a u_j rho u_j + p
-          else if (c == 4) g = tmul(U, taxpy(c_alpha, F, Pt));  // u_j (a rho E + p)
+          else if (c == 4 && !KEEP) g = tmul(U, taxpy(c_alpha, F, Pt));  // u_j (a rho E + p)
           else g = tmul(aU, F);
           suf[c] = suf[c] + dsum(g, c_8);
           if (c == 1 + j) suf[0] = fma(c_alpha, dF, suf[0]);  // D_j(rho u_j)
@@ -565,7 +615,8 @@ __device__ __forceinline__ void stage_tile(const Problem& P, const StageArgs& S,
 #pragma unroll
         for (int i = 0; i < 3; ++i)
           Uall[i] = (i == j) ? U : (i == 2 ? Wt : ((j == 1 && i == 0) ? uy_c : tap(F_U + i)));
-        if constexpr (KGP) kgp_extra(j, U, Uall, F0j, F4j, dFj, fc, uc, c_8, kx);
+        if constexpr (CUBIC) kgp_extra(j, U, Uall, F0j, F4j, dFj, fcc, uc, c_8, kx);
+        if constexpr (KEEP) keep_extra(j, U, Uall, Fmj, Pt, dFj, fc, uc, pc, c_8, c_4, kx);
         // velocity second derivatives (and first derivatives for diagnostics)
 #pragma unroll
         for (int i = 0; i < 3; ++i) {
@@ -599,7 +650,7 @@ __device__ __forceinline__ void stage_tile(const Problem& P, const StageArgs& S,
       V R[5];
 #pragma unroll
       for (int c = 0; c < 5; ++c)
-        R[c] = -(fma(c_inv12h, fma(c_beta, udf[c] + kx[c], suf[c]), c_beta * fc[c] * div));
+        R[c] = -(fma(c_inv12h, fma(c_beta, udf[c] + kx[c], suf[c]), c_beta * fcc[c] * div));
 #pragma unroll
       for (int i = 0; i < 3; ++i)
         R[1 + i] = fma(c_nu, fma(c_inv12h2, d2u[i], c_13 * c_inv12h * ds[i]), R[1 + i]);
@@ -681,11 +732,11 @@ __device__ __forceinline__ void stage_tile(const Problem& P, const StageArgs& S,
 }
 
 template <class TS, class TT, class TC, class TA, int TX, int TY, int NP, int EPI, bool DIAG,
-          bool KGP = false>
+          int SPL = SPL_QUAD>
 __global__ void __launch_bounds__(Geo<TX, TY, NP>::NT, 1)
 stage_kernel(const Problem P, const StageArgs S) {
   const long long cta = ((long long)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
-  stage_tile<TS, TT, TC, TA, TX, TY, NP, EPI, DIAG, KGP>(P, S, blockIdx.x * TX, blockIdx.y * TY,
+  stage_tile<TS, TT, TC, TA, TX, TY, NP, EPI, DIAG, SPL>(P, S, blockIdx.x * TX, blockIdx.y * TY,
                                                          blockIdx.z * S.zchunk, cta);
 }
 

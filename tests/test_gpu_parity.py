@@ -43,7 +43,7 @@ def test_rhs_fp64_matches_oracle(tile, n, field):
     assert max(err) < 1e-11, err
 
 
-@pytest.mark.parametrize("split", ["blaisdell", "divergence", "kgp"])
+@pytest.mark.parametrize("split", ["blaisdell", "divergence", "kgp", "keep"])
 @pytest.mark.parametrize("zchunk", [0, 5, 16])
 def test_rhs_split_forms_and_zchunks(split, zchunk):
     cfg = tgv.Config(n=32, mode="fp64", split=split, zchunk=zchunk, mach=0.3, re=50.0)
@@ -167,10 +167,12 @@ def test_full_size_half_single_stage_sampled(n):
     assert bool(((got - ref).abs() <= 2.0 ** -10 * ref.abs() + bound).all())
 
 
+@pytest.mark.parametrize("split", ["kgp", "keep"])
 @pytest.mark.parametrize("n,tile", [(32, 0), (40, 0), (48, 3)])
-def test_kgp_rhs_and_steps_match_oracle(n, tile):
-    """The cubic KGP split (FP64): residual on a random state, and 5 RK3 steps."""
-    cfg = tgv.Config(n=n, mode="fp64", split="kgp", mach=0.3, re=100.0, tile=tile)
+def test_cubic_rhs_and_steps_match_oracle(n, tile, split):
+    """The cubic KGP and KEEP splits (FP64): residual on a random state, and 5
+    RK3 steps."""
+    cfg = tgv.Config(n=n, mode="fp64", split=split, mach=0.3, re=100.0, tile=tile)
     flow = oracle_flow(cfg)
     q64 = random_state(cfg, seed=17 + n)
     r = torch.empty(5, n, n, n, dtype=torch.float64, device="cuda")
@@ -183,10 +185,24 @@ def test_kgp_rhs_and_steps_match_oracle(n, tile):
     assert max(rel_l2((qb if par else qa).cpu(), ref)) < 1e-12
 
 
-def test_kgp_unsupported_where_not_built():
-    cfg = tgv.Config(n=32, mode="fp16_fp32", split="kgp")
+@pytest.mark.parametrize("split", ["kgp", "keep"])
+def test_cubic_unsupported_where_not_built(split):
+    cfg = tgv.Config(n=32, mode="fp16_fp32", split=split)
     q = tgv.empty_state(cfg)
     r = torch.empty(5, 32, 32, 32, dtype=torch.float32, device="cuda")
     with pytest.raises(tgv.TGVError) as ei:
         tgv.rhs_eval(cfg, q, r)
     assert ei.value.status == tgv._abi.TGV_ERR_UNSUPPORTED
+
+
+@pytest.mark.parametrize("mode", ["fp32", "hpsp"])
+def test_keep_reduced_precision_rhs(mode):
+    """KEEP in the FP32-compute modes of the split-form study: the residual on
+    a random state within FP32 rounding of the oracle (2e-4 of each field's
+    largest value, as for the quadratic forms at this Mach number)."""
+    cfg = tgv.Config(n=32, mode=mode, split="keep", mach=0.3, re=100.0)
+    q64 = random_state(cfg, seed=29)
+    r = torch.empty(5, 32, 32, 32, dtype=torch.float32, device="cuda")
+    tgv.rhs_eval(cfg, encode(cfg, q64), r)
+    ref = oracle.residual(oracle_flow(cfg), decode(cfg, encode(cfg, q64)))
+    assert max(max_rel(r.double().cpu(), ref)) < 2e-4

@@ -98,7 +98,7 @@ def test_residual_converges_at_fourth_order(exact, group):
         assert a / b > 13.0, (group, c, a, b)
 
 
-@pytest.mark.parametrize("split", ["divergence", "kgp"])
+@pytest.mark.parametrize("split", ["divergence", "kgp", "keep"])
 def test_other_split_forms_converge_to_same_rhs(exact, split):
     prim_fns, conv_fns, _, _ = exact
     errs = []
@@ -117,7 +117,7 @@ def _random_state(n, seed, mach=0.3):
     return flow, oracle.conserved(flow, rho, u, v, w, p)
 
 
-@pytest.mark.parametrize("split", ["blaisdell", "divergence", "kgp"])
+@pytest.mark.parametrize("split", ["blaisdell", "divergence", "kgp", "keep"])
 def test_discrete_conservation(split):
     flow, q = _random_state(16, 3)
     flow = flow.with_(split=split)
@@ -188,4 +188,47 @@ def test_kgp_kinetic_energy_identity():
         s = sum(u[i] * conv[1 + i] for i in range(3)) - ke * conv[0]
         return abs(float(s.sum())) / float((u[0] * conv[1]).abs().sum())
     assert imbalance("kgp") < 1e-13, imbalance("kgp")
+    assert imbalance("keep") < 1e-13, imbalance("keep")
     assert imbalance("blaisdell") > 1e-6 and imbalance("divergence") > 1e-6
+
+
+def test_keep_equals_its_two_point_flux_form():
+    """Reading R14 defines KEEP by two-point fluxes; the oracle evaluates an
+    expanded split form.  Pin: the conservative flux difference built here
+    directly from the two-point fluxes,
+        delta_j F = (2/h) sum_(l=1,2) a_l [F(q_i, q_(i+l)) - F(q_(i-l), q_i)],
+        a_1 = 2/3, a_2 = -1/12 (the weights of the 4th-order D),
+    equals the oracle's convective plus pressure terms for all five equations."""
+    flow, q = _random_state(16, 21)
+    flow = flow.with_(split="keep")
+    g1 = flow.gamma - 1.0
+    rho = q[0]
+    vel = [q[1 + i] / rho for i in range(3)]
+    p = g1 * (q[4] - 0.5 * rho * (vel[0] ** 2 + vel[1] ** 2 + vel[2] ** 2))
+    e = p / (g1 * rho)
+    dim = {0: 2, 1: 1, 2: 0}
+
+    def flux(a, b, j):
+        """Two-point KEEP fluxes in direction j between states a and b."""
+        ra, rb = a[0], b[0]
+        ua, ub = a[1 + j], b[1 + j]
+        mass = (ra + rb) * (ua + ub) / 4.0
+        mom = [mass * (a[1 + c] + b[1 + c]) / 2.0 + ((a[4] + b[4]) / 2.0 if c == j else 0.0)
+               for c in range(3)]
+        vv = a[1] * b[1] + a[2] * b[2] + a[3] * b[3]
+        energy = mass * (a[5] + b[5]) / 2.0 + mass * vv / 2.0 + (a[4] * ub + b[4] * ua) / 2.0
+        return [mass] + mom + [energy]
+
+    prim = torch.stack([rho, vel[0], vel[1], vel[2], p, e])   # (rho, u, v, w, p, e)
+    total = torch.zeros_like(q)
+    for j in range(3):
+        sh = lambda f, l: torch.roll(f, -l, dims=1 + dim[j])   # value at i + l
+        for l, a_l in ((1, 2.0 / 3.0), (2, -1.0 / 12.0)):
+            right = flux(prim, sh(prim, l), j)
+            left = flux(sh(prim, -l), prim, j)
+            for c in range(5):
+                total[c] += 2.0 * a_l * (right[c] - left[c]) / flow.h
+    split_form = oracle.convective(flow, q) + oracle.pressure_terms(flow, q)
+    for c in range(5):
+        scale = float(split_form[c].abs().max())
+        assert float((total[c] - split_form[c]).abs().max()) < 1e-12 * scale, c
