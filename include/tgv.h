@@ -55,19 +55,22 @@ typedef enum {
 } tgv_status;
 
 /* Convective split forms (Sec. 2.3.1, Eq. 1; the study of Sec. 4.2):
- * Blaisdell quadratic (default), plain divergence form, KGP cubic, and KEEP
+ * Blaisdell quadratic (default), plain divergence form, the Feiereisen
+ * quadratic form printed in Sec. 2.3.1 (1/2 D_j(rho u_j phi)
+ * + 1/2 (phi D_j(rho u_j) + rho u_j D_j phi)), KGP cubic, and KEEP
  * (kinetic energy and entropy preserving: KGP for mass and momentum; for the
  * energy, KGP of the internal energy, the kinetic-energy split of the
  * two-point flux rho_bar u_bar (u_i u_i)~/2 and the pressure work
- * u_j D_j p + p D_j u_j; the paper cites it without printing it).  KGP and
- * KEEP are built for the FP64, FP32 and Q FP32 / Qt FP16 modes of
- * rk_step/rhs_eval (TGV_ERR_UNSUPPORTED elsewhere, in the adjoint and in the
- * ensemble). */
+ * u_j D_j p + p D_j u_j; the paper cites it without printing it).
+ * Feiereisen, KGP and KEEP are built for the FP64, FP32 and Q FP32 / Qt FP16
+ * modes of rk_step/rhs_eval (TGV_ERR_UNSUPPORTED elsewhere, in the adjoint
+ * and in the ensemble). */
 typedef enum {
   TGV_SPLIT_BLAISDELL = 0,
   TGV_SPLIT_DIVERGENCE = 1,
   TGV_SPLIT_KGP = 2,
-  TGV_SPLIT_KEEP = 3
+  TGV_SPLIT_KEEP = 3,
+  TGV_SPLIT_FEIEREISEN = 4
 } tgv_split;
 typedef enum { TGV_ENC_PLAIN = 0, TGV_ENC_OFFSET = 1 } tgv_encoding;
 

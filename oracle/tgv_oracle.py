@@ -33,7 +33,11 @@ used):
       heat flux q_j = -kappa dT/dx_j, kappa = mu / ((gamma-1) M^2 Pr Re).
   R3  Blaisdell split: C_phi = 1/2 sum_j [ D_j(rho u_j phi) + u_j D_j(rho phi)
       + rho phi D_j u_j ]; pressure terms in divergence form.  The plain
-      divergence form C_phi = sum_j D_j(rho u_j phi) is kept as a foil, and
+      divergence form C_phi = sum_j D_j(rho u_j phi) is kept as a foil, the
+      Feiereisen quadratic split that Sec. 2.3.1 prints as its example,
+        C_phi = sum_j [ 1/2 D_j(rho u_j phi) + 1/2 (phi D_j(rho u_j)
+                + rho u_j D_j phi) ],
+      as a second quadratic form of the study, and
       the cubic Kennedy-Gruber-Pirozzoli split of the robustness study
       (Sec. 4.2) as an alternative:
         C_phi = 1/4 sum_j [ D_j(rho u_j phi) + rho D_j(u_j phi) + u_j D_j(rho phi)
@@ -105,7 +109,7 @@ class Flow:
     re: float = 1600.0
     pr: float = 0.71
     mu: float = 1.0
-    split: str = "blaisdell"  # "divergence" (the foil of Sec. 4.2), "kgp" or "keep" (cubic)
+    split: str = "blaisdell"  # "divergence" (the foil), "feiereisen", "kgp" or "keep" (cubic)
     length: float = 2.0 * math.pi
     offset: float = 0.0       # grid points at (i + offset) h; 0.5 = cell-centred
     symmetric: bool = False   # symmetry planes on every face (reading R13)
@@ -191,7 +195,8 @@ def convective(flow: Flow, q: torch.Tensor) -> torch.Tensor:
     (Sec. 2.3.1, Eq. 1).  Blaisdell split (reading R3):
         C_phi = 1/2 sum_j [ D_j(u_j (rho phi)) + u_j D_j(rho phi) + (rho phi) D_j u_j ],
     using rho u_j phi = u_j (rho phi); (rho phi) are the components of Q.
-    Divergence form: C_phi = sum_j D_j(u_j (rho phi)).  KGP cubic form: the
+    Divergence form: C_phi = sum_j D_j(u_j (rho phi)).  Feiereisen (Sec. 2.3.1):
+    1/2 D_j(rho u_j phi) + 1/2 (phi D_j(rho u_j) + rho u_j D_j phi).  KGP cubic form: the
     seven-term quarter average of reading R3.  KEEP (reading R14): KGP for
     phi = 1 and u_i; for the energy, KGP of the internal energy plus the
     kinetic-energy split (its pressure work is in ``pressure_terms``)."""
@@ -211,6 +216,9 @@ def convective(flow: Flow, q: torch.Tensor) -> torch.Tensor:
                 acc = acc + flux
             elif flow.split == "blaisdell":
                 acc = acc + 0.5 * (flux + vel[j] * d1(f, j, h) + f * d1(vel[j], j, h))
+            elif flow.split == "feiereisen":
+                m_j = q[1 + j]  # rho u_j
+                acc = acc + 0.5 * flux + 0.5 * (phi * d1(m_j, j, h) + m_j * d1(phi, j, h))
             elif flow.split in ("kgp", "keep"):
                 m_j = q[1 + j]  # rho u_j
                 acc = acc + 0.25 * (flux + rho * d1(vel[j] * phi, j, h) + vel[j] * d1(f, j, h)

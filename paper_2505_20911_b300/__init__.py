@@ -80,7 +80,8 @@ class Config:
         return _abi.tgv_config(
             n=self.n,
             split_form={"blaisdell": TGV_SPLIT_BLAISDELL, "divergence": TGV_SPLIT_DIVERGENCE,
-                        "kgp": _abi.TGV_SPLIT_KGP, "keep": _abi.TGV_SPLIT_KEEP}[self.split],
+                        "kgp": _abi.TGV_SPLIT_KGP, "keep": _abi.TGV_SPLIT_KEEP,
+                        "feiereisen": _abi.TGV_SPLIT_FEIEREISEN}[self.split],
             q_storage=qs, qt_storage=qts, compute=comp, accumulate=acc,
             encoding={"plain": TGV_ENC_PLAIN, "offset": TGV_ENC_OFFSET}[self.encoding],
             tile=self.tile, zchunk=self.zchunk,

@@ -17,6 +17,7 @@ TGV_OK = 0
 TGV_ERR_ARG, TGV_ERR_UNSUPPORTED, TGV_ERR_CUDA = -1, -2, -3
 TGV_ERR_NONFINITE, TGV_ERR_UNSTABLE_DT, TGV_ERR_TIMEOUT, TGV_ERR_WORKSPACE = -4, -5, -6, -7
 TGV_SPLIT_BLAISDELL, TGV_SPLIT_DIVERGENCE, TGV_SPLIT_KGP, TGV_SPLIT_KEEP = 0, 1, 2, 3
+TGV_SPLIT_FEIEREISEN = 4
 TGV_ENC_PLAIN, TGV_ENC_OFFSET = 0, 1
 TGV_FLAG_ALLOW_UNSTABLE_DT = 1
 TGV_FLAG_CHECK_FINITE = 2

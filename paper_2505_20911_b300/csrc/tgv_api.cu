@@ -74,7 +74,8 @@ static int32_t check(const tgv_config* c) {
   if (!c) return TGV_ERR_ARG;
   if (c->n < 8 || c->n > 1024 || (c->n & 1)) return TGV_ERR_ARG;
   if (c->split_form != TGV_SPLIT_BLAISDELL && c->split_form != TGV_SPLIT_DIVERGENCE &&
-      c->split_form != TGV_SPLIT_KGP && c->split_form != TGV_SPLIT_KEEP)
+      c->split_form != TGV_SPLIT_KGP && c->split_form != TGV_SPLIT_KEEP &&
+      c->split_form != TGV_SPLIT_FEIEREISEN)
     return TGV_ERR_ARG;
   if (!valid_dtype(c->q_storage) || !valid_dtype(c->qt_storage) || !valid_dtype(c->compute) ||
       !valid_dtype(c->accumulate))
@@ -259,13 +260,11 @@ static int32_t launch_stage_common(const tgv_config* cfg, const StageArgs& S, bo
   A.zchunk = zc;
   const Problem P = make_problem(*cfg);
   if (ctas) *ctas = stage_ctas(*cfg, tile, zc);
-  StageFn fn;
-  if (cfg->split_form == TGV_SPLIT_KGP)
-    fn = rhs ? L.rhs_kgp[tile] : (S.diag_part ? L.stage_kgp_diag[tile] : L.stage_kgp[tile]);
-  else if (cfg->split_form == TGV_SPLIT_KEEP)
-    fn = rhs ? L.rhs_keep[tile] : (S.diag_part ? L.stage_keep_diag[tile] : L.stage_keep[tile]);
-  else
-    fn = rhs ? L.rhs[tile] : (S.diag_part ? L.stage_diag[tile] : L.stage[tile]);
+  const int v = cfg->split_form == TGV_SPLIT_KGP      ? SPL_KGP
+                : cfg->split_form == TGV_SPLIT_KEEP     ? SPL_KEEP
+                : cfg->split_form == TGV_SPLIT_FEIEREISEN ? SPL_FEIER
+                                                         : SPL_QUAD;
+  const StageFn fn = rhs ? L.rhs[v][tile] : (S.diag_part ? L.stage_diag[v][tile] : L.stage[v][tile]);
   if (!fn) return TGV_ERR_UNSUPPORTED;
   cudaError_t e = fn(P, A, zc, st);
   return e == cudaSuccess ? TGV_OK : TGV_ERR_CUDA;

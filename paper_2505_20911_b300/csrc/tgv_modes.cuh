@@ -46,13 +46,13 @@ using OccFn = int (*)();
 using InitFn = cudaError_t (*)(const Problem&, void*, cudaStream_t);
 using DiagFn = cudaError_t (*)(const Problem&, const void*, double*, int, cudaStream_t);
 
+// Kernel variants by convective split family (SPL_QUAD, SPL_KGP, SPL_KEEP,
+// SPL_FEIER); only SPL_QUAD is built for every mode.
+constexpr int NUM_SPL = 4;
 struct ModeLaunchers {
-  StageFn stage[NUM_TILES];      // EPI_RK
-  StageFn stage_diag[NUM_TILES]; // EPI_RK with the fused diagnostics of its input
-  StageFn rhs[NUM_TILES];        // EPI_RHS
-  // the cubic KGP and KEEP splits (null where a mode does not build them)
-  StageFn stage_kgp[NUM_TILES], stage_kgp_diag[NUM_TILES], rhs_kgp[NUM_TILES];
-  StageFn stage_keep[NUM_TILES], stage_keep_diag[NUM_TILES], rhs_keep[NUM_TILES];
+  StageFn stage[NUM_SPL][NUM_TILES];      // EPI_RK (null where a mode does not build it)
+  StageFn stage_diag[NUM_SPL][NUM_TILES]; // EPI_RK with the fused diagnostics of its input
+  StageFn rhs[NUM_SPL][NUM_TILES];        // EPI_RHS
   OccFn occupancy[NUM_TILES];    // resident CTAs per SM of the EPI_RK kernel
   size_t smem[NUM_TILES];        // dynamic shared memory per CTA
   int first_tile = 0;            // tile tried before the table order
@@ -108,28 +108,28 @@ cudaError_t launch_diag_partial(const Problem& P, const void* q, double* part, i
   return cudaGetLastError();
 }
 
+template <class TS, class TT, class TC, class TA, int TX, int TY, int NP, int SPL>
+void set_split(ModeLaunchers& L, int t) {
+  L.stage[SPL][t] = launch_stage<TS, TT, TC, TA, TX, TY, NP, EPI_RK, false, SPL>;
+  L.stage_diag[SPL][t] = launch_stage<TS, TT, TC, TA, TX, TY, NP, EPI_RK, true, SPL>;
+  L.rhs[SPL][t] = launch_stage<TS, TT, TC, TA, TX, TY, NP, EPI_RHS, false, SPL>;
+}
+
 template <class TS, class TT, class TC, class TA, int TX, int TY, int NP, bool WITH_KGP>
 void set_tile(ModeLaunchers& L, int t) {
-  L.stage[t] = launch_stage<TS, TT, TC, TA, TX, TY, NP, EPI_RK, false>;
-  L.stage_diag[t] = launch_stage<TS, TT, TC, TA, TX, TY, NP, EPI_RK, true>;
-  L.rhs[t] = launch_stage<TS, TT, TC, TA, TX, TY, NP, EPI_RHS, false>;
+  for (int v = 0; v < NUM_SPL; ++v) L.stage[v][t] = L.stage_diag[v][t] = L.rhs[v][t] = nullptr;
+  set_split<TS, TT, TC, TA, TX, TY, NP, SPL_QUAD>(L, t);
   if constexpr (WITH_KGP) {
-    L.stage_kgp[t] = launch_stage<TS, TT, TC, TA, TX, TY, NP, EPI_RK, false, SPL_KGP>;
-    L.stage_kgp_diag[t] = launch_stage<TS, TT, TC, TA, TX, TY, NP, EPI_RK, true, SPL_KGP>;
-    L.rhs_kgp[t] = launch_stage<TS, TT, TC, TA, TX, TY, NP, EPI_RHS, false, SPL_KGP>;
-    L.stage_keep[t] = launch_stage<TS, TT, TC, TA, TX, TY, NP, EPI_RK, false, SPL_KEEP>;
-    L.stage_keep_diag[t] = launch_stage<TS, TT, TC, TA, TX, TY, NP, EPI_RK, true, SPL_KEEP>;
-    L.rhs_keep[t] = launch_stage<TS, TT, TC, TA, TX, TY, NP, EPI_RHS, false, SPL_KEEP>;
-  } else {
-    L.stage_kgp[t] = L.stage_kgp_diag[t] = L.rhs_kgp[t] = nullptr;
-    L.stage_keep[t] = L.stage_keep_diag[t] = L.rhs_keep[t] = nullptr;
+    set_split<TS, TT, TC, TA, TX, TY, NP, SPL_KGP>(L, t);
+    set_split<TS, TT, TC, TA, TX, TY, NP, SPL_KEEP>(L, t);
+    set_split<TS, TT, TC, TA, TX, TY, NP, SPL_FEIER>(L, t);
   }
   L.occupancy[t] = stage_occupancy<TS, TT, TC, TA, TX, TY, NP>;
   L.smem[t] = stage_smem_bytes<TS, TT, TC, TX, TY, NP>();
 }
 
-// WITH_KGP: also build the cubic KGP and KEEP splits (the FP64, FP32 and
-// Q FP32 / Qt FP16 modes: the precisions of the paper's split-form study).
+// WITH_KGP: also build the KGP, KEEP and Feiereisen splits (the FP64, FP32
+// and Q FP32 / Qt FP16 modes: the precisions of the paper's split-form study).
 template <class TS, class TT, class TC, class TA, bool WITH_KGP = false>
 ModeLaunchers make_launchers() {
   ModeLaunchers L;

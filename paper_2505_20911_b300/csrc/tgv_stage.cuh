@@ -48,7 +48,9 @@ enum { EPI_RK = 0, EPI_RHS = 1 };
 // (KGP for mass and momentum, the kinetic-energy and entropy preserving
 // energy split of the two-point fluxes rho_bar u_bar e_bar
 // + rho_bar u_bar (u_i u_i)~/2 + (p u)~).
-enum { SPL_QUAD = 0, SPL_KGP = 1, SPL_KEEP = 2 };
+// The Feiereisen quadratic split (printed in Sec. 2.3.1) is the fourth:
+// 1/2 D_j(rho u_j phi) + 1/2 (phi D_j(rho u_j) + rho u_j D_j phi).
+enum { SPL_QUAD = 0, SPL_KGP = 1, SPL_KEEP = 2, SPL_FEIER = 3 };
 
 struct StageArgs {
   const void* q_in;   // Q layout, storage type TS
@@ -152,7 +154,9 @@ template <class T> __device__ __forceinline__ T warp_sum(T v) {
 // of u_j D f_c and f_c D u_j are shared with the quadratic forms):
 //   kx_c += rho D(u_j phi_c) + phi_c D(rho u_j) + (rho u_j) D phi_c + u_j phi_c D rho
 // with phi = (1, u, v, w, E), E = rho E / rho; raw sums, scaled by 1/12h later.
-template <class V>
+// FULL = false keeps only phi D_j(rho u_j) + rho u_j D_j phi (the Feiereisen
+// split's second part).
+template <bool FULL = true, class V>
 __device__ __forceinline__ void kgp_extra(const int j, const Taps<V>& U, const Taps<V>* Ui,
                                           const Taps<V>& F0, const Taps<V>& F4, const V* dF,
                                           const V* fc, const V* uc, const V& c8, V* kx) {
@@ -160,14 +164,19 @@ __device__ __forceinline__ void kgp_extra(const int j, const Taps<V>& U, const T
   const V Ec = fc[4] * rcp(fc[0]);
   const V mj = fc[1 + j];
   // c = 0 (phi = 1): rho D u_j + D(rho u_j) + u_j D rho
-  kx[0] = kx[0] + fma(fc[0], dsum(U, c8), fma(uc[j], dF[0], dF[1 + j]));
+  if constexpr (FULL) kx[0] = kx[0] + fma(fc[0], dsum(U, c8), fma(uc[j], dF[0], dF[1 + j]));
+  else kx[0] = kx[0] + dF[1 + j];
 #pragma unroll
   for (int c = 1; c < 5; ++c) {
     const Taps<V>& Ph = (c == 4) ? Et : Ui[c - 1];
     const V phc = (c == 4) ? Ec : uc[c - 1];
-    const V duphi = dsum(tmul(U, Ph), c8);
     const V dphi = dsum(Ph, c8);
-    kx[c] = kx[c] + fma(fc[0], duphi, fma(phc, dF[1 + j], fma(mj, dphi, uc[j] * phc * dF[0])));
+    if constexpr (FULL) {
+      const V duphi = dsum(tmul(U, Ph), c8);
+      kx[c] = kx[c] + fma(fc[0], duphi, fma(phc, dF[1 + j], fma(mj, dphi, uc[j] * phc * dF[0])));
+    } else {
+      kx[c] = kx[c] + fma(phc, dF[1 + j], mj * dphi);
+    }
   }
 }
 
@@ -226,9 +235,12 @@ __device__ __forceinline__ void stage_tile(const Problem& P, const StageArgs& S,
   const V c_m53 = V::splat(cvt<TC>(-5.0 / 3.0)), c_one = V::splat(cvt<TC>(1.0));
   // convective split: a sum_j D_j(u_j f) + b (sum_j u_j D_j f + f div u) [+ b kx]
   const bool blaisdell = (P.split == TGV_SPLIT_BLAISDELL);
-  constexpr bool CUBIC = SPL != SPL_QUAD, KEEP = SPL == SPL_KEEP;
-  const V c_alpha = V::splat(cvt<TC>(CUBIC ? 0.25 : (blaisdell ? 0.5 : 1.0)));
-  const V c_beta = V::splat(cvt<TC>(CUBIC ? 0.25 : (blaisdell ? 0.5 : 0.0)));
+  constexpr bool CUBIC = SPL == SPL_KGP || SPL == SPL_KEEP, KEEP = SPL == SPL_KEEP;
+  constexpr bool FEIER = SPL == SPL_FEIER, XTRA = SPL != SPL_QUAD;  // XTRA: kgp_extra terms
+  // C = alpha sum_j D_j(u_j f) + beta (sum_j u_j D_j f + f div u) + gamma kx
+  const V c_alpha = V::splat(cvt<TC>(CUBIC ? 0.25 : (FEIER || blaisdell ? 0.5 : 1.0)));
+  const V c_beta = V::splat(cvt<TC>(CUBIC ? 0.25 : (!FEIER && blaisdell ? 0.5 : 0.0)));
+  const V c_gam = V::splat(cvt<TC>(CUBIC ? 0.25 : (FEIER ? 0.5 : 0.0)));
   const V c_ig1 = V::splat(cvt<TC>(1.0 / P.gm1)), c_4 = V::splat(cvt<TC>(4.0));
 
   // ---- region units this thread loads and converts each plane.  Unit q < NT
@@ -496,7 +508,7 @@ __device__ __forceinline__ void stage_tile(const Problem& P, const StageArgs& S,
           const V dF = dsum(F, c_8);
           dFz[c] = dF;
           if (c == 0) F0z = F;
-          if constexpr (CUBIC) {
+          if constexpr (XTRA) {
             if (c == 4) F4z = F;
           }
           if constexpr (KEEP) {
@@ -511,9 +523,9 @@ __device__ __forceinline__ void stage_tile(const Problem& P, const StageArgs& S,
           suf[c] = suf[c] + dsum(g, c_8);
           if (c == 3) suf[0] = fma(c_alpha, dF, suf[0]);  // D_z(rho w)
         }
-        if constexpr (CUBIC) {
+        if constexpr (XTRA) {
           const Taps<V> UZall[3] = {uz, vz, wz};
-          kgp_extra(2, U, UZall, F0z, F4z, dFz, fcc, uc, c_8, kx);
+          kgp_extra<!FEIER>(2, U, UZall, F0z, F4z, dFz, fcc, uc, c_8, kx);
           if constexpr (KEEP) keep_extra(2, U, UZall, Fmz, Pt, dFz, fc, uc, pc, c_8, c_4, kx);
         }
         const Taps<V>* UZ[3] = {&uz, &vz, &wz};
@@ -596,7 +608,7 @@ __device__ __forceinline__ void stage_tile(const Problem& P, const StageArgs& S,
           const V dF = dsum(F, c_8);
           dFj[c] = dF;
           if (c == 0) F0j = F;
-          if constexpr (CUBIC) {
+          if constexpr (XTRA) {
             if (c == 4) F4j = F;
           }
           if constexpr (KEEP) {
@@ -615,7 +627,7 @@ __device__ __forceinline__ void stage_tile(const Problem& P, const StageArgs& S,
 #pragma unroll
         for (int i = 0; i < 3; ++i)
           Uall[i] = (i == j) ? U : (i == 2 ? Wt : ((j == 1 && i == 0) ? uy_c : tap(F_U + i)));
-        if constexpr (CUBIC) kgp_extra(j, U, Uall, F0j, F4j, dFj, fcc, uc, c_8, kx);
+        if constexpr (XTRA) kgp_extra<!FEIER>(j, U, Uall, F0j, F4j, dFj, fcc, uc, c_8, kx);
         if constexpr (KEEP) keep_extra(j, U, Uall, Fmj, Pt, dFj, fc, uc, pc, c_8, c_4, kx);
         // velocity second derivatives (and first derivatives for diagnostics)
 #pragma unroll
@@ -650,7 +662,8 @@ __device__ __forceinline__ void stage_tile(const Problem& P, const StageArgs& S,
       V R[5];
 #pragma unroll
       for (int c = 0; c < 5; ++c)
-        R[c] = -(fma(c_inv12h, fma(c_beta, udf[c] + kx[c], suf[c]), c_beta * fcc[c] * div));
+        R[c] = -(fma(c_inv12h, fma(c_beta, udf[c], XTRA ? fma(c_gam, kx[c], suf[c]) : suf[c]),
+                     c_beta * fcc[c] * div));
 #pragma unroll
       for (int i = 0; i < 3; ++i)
         R[1 + i] = fma(c_nu, fma(c_inv12h2, d2u[i], c_13 * c_inv12h * ds[i]), R[1 + i]);

@@ -2,11 +2,12 @@
 dt = 0.004, viscous terms off) and the non-finite stop of rk_step.
 
 The paper reports that the plain divergence form diverges quickly while the
-quadratic split forms (Blaisdell among them) keep the kinetic energy near
-its initial value much longer, in double and in half-single precision alike.
+quadratic split forms (Blaisdell and Feiereisen among them) keep the kinetic
+energy near its initial value much longer, in double and in half-single
+precision alike.
 It also reports that the cubic KGP and KEEP splits stay stable up to t = 20.
-Checked here: the Blaisdell form keeps K/K0 within 1e-2 of 1 at least as long
-as the divergence form does, KGP and KEEP stay finite to t = 20 and keep K/K0
+Checked here: the Blaisdell and Feiereisen forms keep K/K0 within 1e-2 of 1
+at least as long as the divergence form does, KGP and KEEP stay finite to t = 20 and keep K/K0
 within 1e-2 at least as long as Blaisdell, in FP64 and in the Q FP32 / Qt FP16
 mode; and the first non-finite state stops rk_step with TGV_ERR_NONFINITE.
 """
@@ -58,13 +59,15 @@ def test_split_forms_in_the_inviscid_limit(mode):
     r_d, nan_d = _history(mode, "divergence")
     r_k, nan_k = _history(mode, "kgp")
     r_e, nan_e = _history(mode, "keep")
+    r_f, nan_f = _history(mode, "feiereisen")
     t_b, t_d, t_k = _time_within(r_b), _time_within(r_d), _time_within(r_k)
-    t_e = _time_within(r_e)
+    t_e, t_f = _time_within(r_e), _time_within(r_f)
     print(f"\n{mode}: K/K0 within 1e-2 until t = {t_d:.2f} divergence (non-finite {nan_d}), "
+          f"{t_f:.2f} Feiereisen (non-finite {nan_f}), "
           f"{t_b:.2f} Blaisdell (non-finite {nan_b}), {t_k:.2f} KGP (non-finite {nan_k}), "
-          f"{t_e:.2f} KEEP (non-finite {nan_e}); K/K0 at the end: Blaisdell {r_b[-1]:.4f}, "
-          f"KGP {r_k[-1]:.4f}, KEEP {r_e[-1]:.4f}")
-    assert t_b >= t_d
+          f"{t_e:.2f} KEEP (non-finite {nan_e}); K/K0 at the end: Feiereisen {r_f[-1]:.4f}, "
+          f"Blaisdell {r_b[-1]:.4f}, KGP {r_k[-1]:.4f}, KEEP {r_e[-1]:.4f}")
+    assert t_b >= t_d and t_f >= t_d
     assert not nan_k and t_k >= t_b
     assert not nan_e and t_e >= t_b
     assert r_b[int(1.0 / (EVERY * DT))] == pytest.approx(1.0, abs=2e-3)  # t = 1

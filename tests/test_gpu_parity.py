@@ -43,7 +43,7 @@ def test_rhs_fp64_matches_oracle(tile, n, field):
     assert max(err) < 1e-11, err
 
 
-@pytest.mark.parametrize("split", ["blaisdell", "divergence", "kgp", "keep"])
+@pytest.mark.parametrize("split", ["blaisdell", "divergence", "feiereisen", "kgp", "keep"])
 @pytest.mark.parametrize("zchunk", [0, 5, 16])
 def test_rhs_split_forms_and_zchunks(split, zchunk):
     cfg = tgv.Config(n=32, mode="fp64", split=split, zchunk=zchunk, mach=0.3, re=50.0)
@@ -167,11 +167,11 @@ def test_full_size_half_single_stage_sampled(n):
     assert bool(((got - ref).abs() <= 2.0 ** -10 * ref.abs() + bound).all())
 
 
-@pytest.mark.parametrize("split", ["kgp", "keep"])
+@pytest.mark.parametrize("split", ["feiereisen", "kgp", "keep"])
 @pytest.mark.parametrize("n,tile", [(32, 0), (40, 0), (48, 3)])
-def test_cubic_rhs_and_steps_match_oracle(n, tile, split):
-    """The cubic KGP and KEEP splits (FP64): residual on a random state, and 5
-    RK3 steps."""
+def test_study_splits_rhs_and_steps_match_oracle(n, tile, split):
+    """The Feiereisen, KGP and KEEP splits of the study (FP64): residual on a
+    random state, and 5 RK3 steps."""
     cfg = tgv.Config(n=n, mode="fp64", split=split, mach=0.3, re=100.0, tile=tile)
     flow = oracle_flow(cfg)
     q64 = random_state(cfg, seed=17 + n)
@@ -185,8 +185,8 @@ def test_cubic_rhs_and_steps_match_oracle(n, tile, split):
     assert max(rel_l2((qb if par else qa).cpu(), ref)) < 1e-12
 
 
-@pytest.mark.parametrize("split", ["kgp", "keep"])
-def test_cubic_unsupported_where_not_built(split):
+@pytest.mark.parametrize("split", ["feiereisen", "kgp", "keep"])
+def test_study_splits_unsupported_where_not_built(split):
     cfg = tgv.Config(n=32, mode="fp16_fp32", split=split)
     q = tgv.empty_state(cfg)
     r = torch.empty(5, 32, 32, 32, dtype=torch.float32, device="cuda")

@@ -61,7 +61,7 @@ def test_symmetric_box_is_one_octant_of_the_periodic_run(mode):
     assert max(rel_l2(out[0], out[1][:, :n, :n, :n])) < tol
 
 
-@pytest.mark.parametrize("split", ["kgp", "keep", "divergence"])
+@pytest.mark.parametrize("split", ["kgp", "keep", "feiereisen", "divergence"])
 def test_symmetric_box_with_other_split_forms(split):
     """The mirror ghosts are independent of the convective split: the KGP and
     divergence forms in the symmetric box against the oracle (FP64)."""

@@ -98,7 +98,7 @@ def test_residual_converges_at_fourth_order(exact, group):
         assert a / b > 13.0, (group, c, a, b)
 
 
-@pytest.mark.parametrize("split", ["divergence", "kgp", "keep"])
+@pytest.mark.parametrize("split", ["divergence", "feiereisen", "kgp", "keep"])
 def test_other_split_forms_converge_to_same_rhs(exact, split):
     prim_fns, conv_fns, _, _ = exact
     errs = []
@@ -117,7 +117,7 @@ def _random_state(n, seed, mach=0.3):
     return flow, oracle.conserved(flow, rho, u, v, w, p)
 
 
-@pytest.mark.parametrize("split", ["blaisdell", "divergence", "kgp", "keep"])
+@pytest.mark.parametrize("split", ["blaisdell", "divergence", "feiereisen", "kgp", "keep"])
 def test_discrete_conservation(split):
     flow, q = _random_state(16, 3)
     flow = flow.with_(split=split)
@@ -190,6 +190,19 @@ def test_kgp_kinetic_energy_identity():
     assert imbalance("kgp") < 1e-13, imbalance("kgp")
     assert imbalance("keep") < 1e-13, imbalance("keep")
     assert imbalance("blaisdell") > 1e-6 and imbalance("divergence") > 1e-6
+
+
+def test_feiereisen_skew_part_is_zero_sum_and_linear_case():
+    """Feiereisen (Sec. 2.3.1): the part 1/2 (phi D(rho u) + rho u D phi) sums
+    to zero over the periodic box (D is skew), and with phi constant (the
+    mass equation) the split reduces to the divergence form D(rho u_j)."""
+    flow, q = _random_state(16, 13)
+    conv_f = oracle.convective(flow.with_(split="feiereisen"), q)
+    conv_d = oracle.convective(flow.with_(split="divergence"), q)
+    assert torch.allclose(conv_f[0], conv_d[0], rtol=0, atol=1e-12 * float(conv_d[0].abs().max()))
+    for c in range(1, 5):
+        skew = 2.0 * (conv_f[c] - 0.5 * conv_d[c])
+        assert abs(float(skew.sum())) < 1e-12 * float(skew.abs().sum()), c
 
 
 def test_keep_equals_its_two_point_flux_form():
