@@ -56,11 +56,38 @@ template <> struct Cvt<float, __nv_bfloat16> {
 template <> struct Cvt<__nv_bfloat16, float> {
   static __device__ __forceinline__ __nv_bfloat16 go(float v) { return __float2bfloat16_rn(v); }
 };
+// FP64 <-> FP32 conversions in integer arithmetic (IEEE 754 binary64 and
+// binary32 bit layouts; round to nearest, ties to even).  On B300 the
+// hardware conversions share the FP64 pipe, which runs at 1/64 of the FP32
+// rate; these run on the integer pipes.  Values below the FP32 normal range
+// (|x| < 2^-126) become signed zeros.
+__device__ __forceinline__ float f64_to_f32(double x) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  const unsigned hi = (unsigned)(b >> 32), lo = (unsigned)b;
+  const unsigned s = hi & 0x80000000u;
+  const unsigned e = (hi >> 20) & 0x7FFu;               // biased binary64 exponent
+  const unsigned m = ((hi & 0xFFFFFu) << 3) | (lo >> 29);  // top 23 fraction bits
+  const unsigned rem = lo & 0x1FFFFFFFu;                // the 29 dropped bits
+  unsigned f = s | ((e - 896u) << 23) | m;               // rebias 1023 -> 127
+  f += (rem > 0x10000000u || (rem == 0x10000000u && (f & 1u))) ? 1u : 0u;
+  if (e <= 896u) f = s;                                   // below the normal range
+  if (e >= 1151u) f = s | 0x7F800000u | (e == 2047u && (m | rem) ? 0x400000u : 0u);
+  return __uint_as_float(f);
+}
+__device__ __forceinline__ double f32_to_f64(float x) {
+  const unsigned f = __float_as_uint(x);
+  const unsigned s = f & 0x80000000u, e = (f >> 23) & 0xFFu, m = f & 0x7FFFFFu;
+  unsigned hi = s | ((e + 896u) << 20) | (m >> 3);
+  if (e == 0u) hi = s;                                    // zero (subnormals flushed)
+  if (e == 255u) hi = s | 0x7FF00000u | (m >> 3) | (m ? 0x80000u : 0u);
+  const unsigned lo = (e == 0u) ? 0u : (m << 29);
+  return __longlong_as_double((long long)(((unsigned long long)hi << 32) | lo));
+}
 template <> struct Cvt<float, double> {
-  static __device__ __forceinline__ float go(double v) { return (float)v; }
+  static __device__ __forceinline__ float go(double v) { return f64_to_f32(v); }
 };
 template <> struct Cvt<double, float> {
-  static __device__ __forceinline__ double go(float v) { return (double)v; }
+  static __device__ __forceinline__ double go(float v) { return f32_to_f64(v); }
 };
 template <class To, class From>
 __device__ __forceinline__ To cvt(From v) { return Cvt<To, From>::go(v); }
