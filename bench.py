@@ -57,6 +57,10 @@ def parse():
                     help="default: 2000 (tgv), 8000 = t 20 (tgsym)")
     ap.add_argument("--accuracy-modes", default=None,
                     help="comma-separated subset of the sweep's modes (default: all)")
+    ap.add_argument("--accuracy-dt", type=float, default=None, help="override dt")
+    ap.add_argument("--accuracy-mach", type=float, default=None, help="override the Mach number")
+    ap.add_argument("--accuracy-t-end", type=float, default=None,
+                    help="run to this time (steps = t_end / dt) instead of --accuracy-steps")
     ap.add_argument("--accuracy-workload", default="tgv", choices=["tgv", "tgsym"],
                     help="tgv: periodic 2 pi box, M 0.1, Re 1600, dt 0.00125 at 256^3; tgsym: "
                          "the symmetric pi box of Sec. 4.1/4.3, M 0.5, Re 800, dt 0.0025")
@@ -97,14 +101,19 @@ def accuracy_sweep(args):
     import paper_2505_20911_b300 as tgv
     sym = args.accuracy_workload == "tgsym"
     n = args.n
-    steps = args.accuracy_steps or (8000 if sym else 2000)
-    dt = 0.0025 if sym else DT_DEFAULT * 256.0 / n
+    dt = args.accuracy_dt or (0.0025 if sym else DT_DEFAULT * 256.0 / n)
+    if args.accuracy_t_end:
+        steps = int(round(args.accuracy_t_end / dt))
+    else:
+        steps = args.accuracy_steps or (8000 if sym else 2000)
+    mach = args.accuracy_mach or (0.5 if sym else 0.1)
     nrec = steps // DIAG_EVERY + 1
 
     def run(mode, encoding=None):
         cfg = mode_config(tgv, n, mode)
         if sym:
-            cfg = cfg.with_(length=math.pi, symmetric=True, mach=0.5, re=800.0)
+            cfg = cfg.with_(length=math.pi, symmetric=True, re=800.0)
+        cfg = cfg.with_(mach=mach)
         if encoding:
             cfg = cfg.with_(encoding=encoding)
         qa = tgv.empty_state(cfg)
@@ -129,7 +138,7 @@ def accuracy_sweep(args):
     d_ref = diss(K_ref)
     per = max(1, int(round(0.5 / (DIAG_EVERY * dt))))
     at = lambda a: a[per - 1::per]       # -dK/dt samples at t = 0.5, 1, ... (index shift 1)
-    out = {"workload": args.accuracy_workload, "n": n, "steps": steps, "dt": dt,
+    out = {"workload": args.accuracy_workload, "n": n, "steps": steps, "dt": dt, "mach": mach,
            "t_end": steps * dt, "reference": "fp64 GPU", "reference_seconds": el_ref,
            "modes": {}}
     # the FP64-compute mode costs a second FP64 run; the paper's TGSym study has no such mode

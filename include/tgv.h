@@ -2,9 +2,11 @@
  * tgv.h - C ABI of the B300 (sm_103a) Taylor-Green-vortex hot path.
  *
  * The library advances the compressible Navier-Stokes equations on a periodic
- * N^3 grid with explicit 4th-order central differences (arXiv 2505.20911,
- * Sec. 2.3.1) and the low-storage 3-stage Runge-Kutta scheme of Sec. 3.1,
- * Eqs. 3-5, starting from the Taylor-Green field of Sec. 4.1, Eqs. 6-10.
+ * N^3 grid (or the mirror-symmetric box of the paper's TGSym runs, see
+ * TGV_FLAG_SYMMETRIC) with explicit 4th-order central differences
+ * (arXiv 2505.20911, Sec. 2.3.1) and the low-storage 3-stage Runge-Kutta
+ * scheme of Sec. 3.1, Eqs. 3-5, starting from the Taylor-Green field of
+ * Sec. 4.1, Eqs. 6-10.
  *
  * Conventions shared by every entry point
  *  - Layout: a state Q is 5 planar fields (rho, rho*u, rho*v, rho*w, rho*E),
@@ -107,7 +109,7 @@ typedef enum { TGV_ENC_PLAIN = 0, TGV_ENC_OFFSET = 1 } tgv_encoding;
  * Anything else returns TGV_ERR_UNSUPPORTED.
  */
 typedef struct tgv_config {
-  int32_t n;          /* N: grid points per direction, 8..1024 (any value) */
+  int32_t n;          /* N: grid points per direction, even, 8..1024          */
   int32_t split_form; /* tgv_split                                            */
   int32_t q_storage;  /* tgv_dtype of Q                                       */
   int32_t qt_storage; /* tgv_dtype of Qt                                      */
