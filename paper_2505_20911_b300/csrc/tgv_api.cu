@@ -283,7 +283,7 @@ int32_t rhs_eval(const tgv_config* cfg, const void* q, void* r, void* stream) {
 
 static int32_t substep_impl(const tgv_config* cfg, const void* q_in, void* q_out, void* qt,
                             int32_t i, double dt, double* diag_part, long long* ctas,
-                            void* stream, bool write_qt = true) {
+                            void* stream, bool write_qt = true, bool scaled_qt = false) {
   StageArgs S;
   std::memset(&S, 0, sizeof(S));
   S.q_in = q_in;
@@ -295,6 +295,8 @@ static int32_t substep_impl(const tgv_config* cfg, const void* q_in, void* q_out
   S.dt = dt;
   S.read_qt = (i != 0);
   S.write_qt = write_qt ? 1 : 0;
+  S.scaled_qt = scaled_qt ? 1 : 0;
+  S.bdt = RK_B[i] * dt;
   return launch_stage_common(cfg, S, false, (cudaStream_t)stream, ctas);
 }
 
@@ -349,7 +351,7 @@ int32_t rk_step(const tgv_config* cfg, void* q_a, void* q_b, void* qt, double dt
       long long ctas = 0;
       double* part = (log && i == 0) ? static_cast<double*>(workspace) : nullptr;
       // the last substep's Qt is never read (A_1 = 0 restarts it): not stored
-      s = substep_impl(cfg, buf[cur], buf[cur ^ 1], qt, i, dt, part, &ctas, stream, i != 2);
+      s = substep_impl(cfg, buf[cur], buf[cur ^ 1], qt, i, dt, part, &ctas, stream, i != 2, true);
       if (s != TGV_OK) return s;
       if (part) {
         double* record = diag_dev + (size_t)rec * TGV_DIAG_COUNT;

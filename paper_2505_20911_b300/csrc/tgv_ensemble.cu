@@ -61,6 +61,8 @@ ensemble_stage_kernel(const EnsTable T, const double a, const double b, const in
     S.dt = I.dt;
     S.read_qt = read_qt;
     S.write_qt = write_qt;
+    S.scaled_qt = 1;  // as rk_step: Qt is internal scratch kept divided by dt
+    S.bdt = b * I.dt;
     S.zchunk = I.zchunk;
     stage_tile<float, float, float, float, TX, TY, 2, EPI_RK, false>(I.P, S, bx * TX, by * TY,
                                                                       bz * I.zchunk, 0);

@@ -61,6 +61,10 @@ struct StageArgs {
   double a, b, dt;    // A_i, B_i, dt
   int read_qt;        // 0 when A_i == 0
   int write_qt;       // 0 on the last substep
+  int scaled_qt;      // 1: the increment is kept divided by dt (W = Qt/dt:
+                      //    W <- A W + R, Q <- Q + (B dt) W), saving the dt
+                      //    multiply; rk_step's Qt is internal scratch
+  double bdt;         // B_i * dt (scaled_qt)
   int zchunk;         // z planes per CTA
 };
 
@@ -705,6 +709,7 @@ __device__ __forceinline__ void stage_tile(const Problem& P, const StageArgs& S,
         TS* q_out = static_cast<TS*>(S.q_out);
         TT* qt = static_cast<TT*>(S.qt);
         const TA a = cvt<TA>(S.a), b = cvt<TA>(S.b), dt = cvt<TA>(S.dt);
+        const TA bdt = cvt<TA>(S.bdt);
         if (S.read_qt) cp_async_wait<1>();  // this plane's Qt group has landed
         const RawT* qts = stage_t + (k & 1) * 5 * NT;
 #pragma unroll
@@ -714,10 +719,17 @@ __device__ __forceinline__ void stage_tile(const Problem& P, const StageArgs& S,
           if (S.read_qt) raw_elems<TA, NP>(qts[c * NT + tid], qold);
 #pragma unroll
           for (int e = 0; e < NP; ++e) {
-            TA v = dt * cvt<TA>(R[c].get(e));
-            if (S.read_qt) v = a * qold[e] + v;
-            qtn[e] = v;
-            qo[e] = qin[e] + b * v;
+            if (S.scaled_qt) {
+              TA v = cvt<TA>(R[c].get(e));
+              if (S.read_qt) v = a * qold[e] + v;
+              qtn[e] = v;
+              qo[e] = qin[e] + bdt * v;
+            } else {
+              TA v = dt * cvt<TA>(R[c].get(e));
+              if (S.read_qt) v = a * qold[e] + v;
+              qtn[e] = v;
+              qo[e] = qin[e] + b * v;
+            }
           }
           UnitStore<TS, NP>::put(q_out + o + c * n3, qo);
           if (S.write_qt) UnitStore<TT, NP>::put(qt + o + c * n3, qtn);
