@@ -97,6 +97,10 @@ __device__ __forceinline__ double recip(double v) { return 1.0 / v; }
 __device__ __forceinline__ float recip(float v) { return 1.0f / v; }
 __device__ __forceinline__ __half recip(__half v) { return hrcp(v); }
 
+// Fused multiply-add a*b + c with one rounding, in the accumulate type.
+__device__ __forceinline__ float fma_rn(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+__device__ __forceinline__ double fma_rn(double a, double b, double c) { return __fma_rn(a, b, c); }
+
 template <class T> __device__ __forceinline__ bool finite_val(T v) {
   double d = Num<T>::to_f64(v);
   return isfinite(d);

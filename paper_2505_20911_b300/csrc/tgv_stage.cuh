@@ -719,16 +719,18 @@ __device__ __forceinline__ void stage_tile(const Problem& P, const StageArgs& S,
           if (S.read_qt) raw_elems<TA, NP>(qts[c * NT + tid], qold);
 #pragma unroll
           for (int e = 0; e < NP; ++e) {
+            // explicit fused multiply-adds: the same rounding in every kernel
+            // that inlines this epilogue (rk_step's and the ensemble's)
             if (S.scaled_qt) {
               TA v = cvt<TA>(R[c].get(e));
-              if (S.read_qt) v = a * qold[e] + v;
+              if (S.read_qt) v = fma_rn(a, qold[e], v);
               qtn[e] = v;
-              qo[e] = qin[e] + bdt * v;
+              qo[e] = fma_rn(bdt, v, qin[e]);
             } else {
               TA v = dt * cvt<TA>(R[c].get(e));
-              if (S.read_qt) v = a * qold[e] + v;
+              if (S.read_qt) v = fma_rn(a, qold[e], v);
               qtn[e] = v;
-              qo[e] = qin[e] + b * v;
+              qo[e] = fma_rn(b, v, qin[e]);
             }
           }
           UnitStore<TS, NP>::put(q_out + o + c * n3, qo);
