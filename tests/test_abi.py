@@ -53,6 +53,17 @@ def test_invalid_configs_are_rejected_on_host():
     assert _abi.lib().tgv_check_config(None) == _abi.TGV_ERR_ARG
 
 
+@pytest.mark.parametrize("split", ["blaisdell", "divergence", "feiereisen", "kgp", "keep"])
+def test_every_split_form_is_a_valid_config(split):
+    assert tgv.tgv_check_config(tgv.Config(n=32, split=split)) == 0
+
+
+def test_unknown_split_form_is_rejected():
+    cfg = tgv.Config(n=32).c()
+    cfg.split_form = 5
+    assert _abi.lib().tgv_check_config(C.byref(cfg)) == _abi.TGV_ERR_ARG
+
+
 def test_null_pointers_fail_before_any_cuda_call():
     cfg = tgv.Config(n=32).c()
     lib = _abi.lib()
