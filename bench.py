@@ -505,6 +505,25 @@ def extra_workloads(args, tgv, torch, dev, stream, peaks):
         torch.cuda.empty_cache()
     out["tgsym_256"] = tgs
 
+    # small grids are launch-bound: 32^3 FP32 per step, direct launches against
+    # a CUDA graph of 10 rk_step steps captured by the caller
+    cfg = tgv.Config(n=32, mode="fp32")
+    qa = tgv.empty_state(cfg)
+    qb, qt = torch.empty_like(qa), tgv.empty_qt(cfg)
+    tgv.tgv_init(cfg, qa)
+    dt32 = 0.5 * tgv.tgv_dt_max(cfg)
+    tgv.rk_step(cfg, qa, qb, qt, dt32, 4, 0, None, None, stream)
+    direct_ms = ev_time(lambda: tgv.rk_step(cfg, qa, qb, qt, dt32, 100, 0, None, None, stream)) / 100
+    side = torch.cuda.Stream()
+    side.wait_stream(torch.cuda.current_stream())
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph, stream=side):
+        tgv.rk_step(cfg, qa, qb, qt, dt32, 10, 0, None, None, side)
+    graph_ms = ev_time(lambda: [graph.replay() for _ in range(10)]) / 100
+    out["graph_32"] = {"direct_ms_per_step": direct_ms, "graph_ms_per_step": graph_ms,
+                       "speedup": direct_ms / graph_ms}
+    del qa, qb, qt, graph
+
     # adjoint: 64^3, 200 steps, checkpoint every 20
     adj = {}
     for mode in ("fp64", "fp32"):
@@ -647,7 +666,7 @@ def main():
                 config=config, roofline=res["roofline"], e2e=res["e2e"],
                 gpu_launches=res["gpu_launches"], clocks=res["clocks"], modes=res["modes"],
                 diag_last=res["diag_last"])
-    for key in ("n512", "tgsym_256", "adjoint_64", "ensemble_48"):
+    for key in ("n512", "tgsym_256", "graph_32", "adjoint_64", "ensemble_48"):
         if key in res:
             line[key] = res[key]
     if world == 1 and not args.no_cpu:
