@@ -195,12 +195,13 @@ def test_study_splits_unsupported_where_not_built(split):
     assert ei.value.status == tgv._abi.TGV_ERR_UNSUPPORTED
 
 
+@pytest.mark.parametrize("split", ["feiereisen", "kgp", "keep"])
 @pytest.mark.parametrize("mode", ["fp32", "hpsp"])
-def test_keep_reduced_precision_rhs(mode):
-    """KEEP in the FP32-compute modes of the split-form study: the residual on
-    a random state within FP32 rounding of the oracle (2e-4 of each field's
+def test_study_splits_reduced_precision_rhs(mode, split):
+    """The study's split forms in its FP32-compute modes: the residual on a
+    random state within FP32 rounding of the oracle (2e-4 of each field's
     largest value, as for the quadratic forms at this Mach number)."""
-    cfg = tgv.Config(n=32, mode=mode, split="keep", mach=0.3, re=100.0)
+    cfg = tgv.Config(n=32, mode=mode, split=split, mach=0.3, re=100.0)
     q64 = random_state(cfg, seed=29)
     r = torch.empty(5, 32, 32, 32, dtype=torch.float32, device="cuda")
     tgv.rhs_eval(cfg, encode(cfg, q64), r)
