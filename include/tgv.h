@@ -315,6 +315,32 @@ int32_t tgv_run_host(const tgv_config* cfg, const void* q_host_in, void* q_host_
                      double dt, int32_t nsteps, int32_t diag_every, double* diag_host,
                      void* dev_workspace, size_t ws_bytes, void* stream);
 
+/*
+ * `count` independent states from host memory, each advanced exactly as by
+ * tgv_run_host (H2D of Q, nsteps RK3 steps with diagnostics every diag_every,
+ * D2H of Q and of its records), with the copies overlapped with computation:
+ * state i is copied in and state i-1 out on copy_stream while the steps run on
+ * compute_stream, through two device buffer sets used in turn.  No paper
+ * counterpart (a pipeline for many runs, e.g. an ensemble of initial fields
+ * held on the host).
+ * q_host_in[i], q_host_out[i]: host, Q layout, q_storage (pinned for the
+ *   copies to overlap); in and out may be the same buffer.
+ * diag_host: nullable; count consecutive blocks of
+ *   (nsteps/diag_every + 1) * TGV_DIAG_COUNT doubles.
+ * dev_workspace: tgv_run_host_stream_workspace_bytes(cfg, nsteps, diag_every)
+ *   bytes (two tgv_run_host workspaces).
+ * compute_stream, copy_stream: may be equal (then nothing overlaps).  Four
+ *   CUDA events are created and destroyed inside the call.  Returns after both
+ *   streams are synchronised; on an error the results of later states are
+ *   not written.
+ */
+size_t tgv_run_host_stream_workspace_bytes(const tgv_config* cfg, int32_t nsteps,
+                                           int32_t diag_every);
+int32_t tgv_run_host_stream(const tgv_config* cfg, int32_t count, const void* const* q_host_in,
+                            void* const* q_host_out, double dt, int32_t nsteps,
+                            int32_t diag_every, double* diag_host, void* dev_workspace,
+                            size_t ws_bytes, void* compute_stream, void* copy_stream);
+
 #ifdef __cplusplus
 }
 #endif

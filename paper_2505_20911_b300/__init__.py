@@ -212,6 +212,35 @@ def tgv_run_host(cfg: Config, q_host_in, q_host_out, dt: float, nsteps: int,
                              _ptr(dev_workspace), ws_bytes, _stream(stream)), "tgv_run_host")
 
 
+def tgv_run_host_stream_workspace_bytes(cfg: Config, nsteps: int, diag_every: int) -> int:
+    return lib().tgv_run_host_stream_workspace_bytes(C.byref(cfg.c()), int(nsteps),
+                                                     int(diag_every))
+
+
+def tgv_run_host_stream(cfg: Config, qs_host_in, qs_host_out, dt: float, nsteps: int,
+                        diag_every: int = 0, diag_host=None, dev_workspace=None,
+                        compute_stream=None, copy_stream=None) -> None:
+    """Several independent states from host (CPU, ideally pinned) tensors, the
+    copies overlapped with the steps on a second stream (tgv_run_host_stream)."""
+    qs_host_in, qs_host_out = list(qs_host_in), list(qs_host_out)
+    if len(qs_host_in) != len(qs_host_out):
+        raise ValueError("as many output buffers as input buffers")
+    for t in qs_host_in + qs_host_out + ([diag_host] if diag_host is not None else []):
+        if t.is_cuda or not t.is_contiguous():
+            raise ValueError("host buffers must be contiguous CPU tensors")
+    count = len(qs_host_in)
+    arr_in = (C.c_void_p * max(count, 1))(*[q.data_ptr() for q in qs_host_in])
+    arr_out = (C.c_void_p * max(count, 1))(*[q.data_ptr() for q in qs_host_out])
+    ws_bytes = dev_workspace.numel() * dev_workspace.element_size()
+    if copy_stream is None:
+        raise ValueError("copy_stream is required (a stream other than the compute stream)")
+    check(lib().tgv_run_host_stream(C.byref(cfg.c()), count, arr_in, arr_out, float(dt),
+                                    int(nsteps), int(diag_every),
+                                    diag_host.data_ptr() if diag_host is not None else None,
+                                    _ptr(dev_workspace), ws_bytes, _stream(compute_stream),
+                                    _stream(copy_stream)), "tgv_run_host_stream")
+
+
 def diagnostics(cfg: Config, q: torch.Tensor, workspace=None) -> dict:
     """Convenience: diagnostics_reduce into a fresh tensor, returned as a dict."""
     ws = workspace if workspace is not None else empty_workspace(cfg, q.device)

@@ -81,6 +81,10 @@ SIGNATURES = {
     "tgv_run_host_workspace_bytes": (C.c_size_t, [_CFG, C.c_int32, C.c_int32]),
     "tgv_run_host": (C.c_int32, [_CFG, _P, _P, C.c_double, C.c_int32, C.c_int32, _P, _P,
                                  C.c_size_t, _P]),
+    "tgv_run_host_stream_workspace_bytes": (C.c_size_t, [_CFG, C.c_int32, C.c_int32]),
+    "tgv_run_host_stream": (C.c_int32, [_CFG, C.c_int32, C.POINTER(C.c_void_p),
+                                        C.POINTER(C.c_void_p), C.c_double, C.c_int32, C.c_int32,
+                                        _P, _P, C.c_size_t, _P, _P]),
 }
 
 

@@ -5,6 +5,7 @@
 #include <cmath>
 #include <cstring>
 #include <atomic>
+#include <vector>
 
 #include "tgv_modes.cuh"
 
@@ -430,6 +431,82 @@ int32_t tgv_run_host(const tgv_config* cfg, const void* q_host_in, void* q_host_
                                  cudaMemcpyDeviceToHost, st));
   TGV_CUDA_TRY(cudaStreamSynchronize(st));
   return TGV_OK;
+}
+
+size_t tgv_run_host_stream_workspace_bytes(const tgv_config* cfg, int32_t nsteps,
+                                           int32_t diag_every) {
+  const size_t one = tgv_run_host_workspace_bytes(cfg, nsteps, diag_every);
+  return one ? 2 * up256(one) : 0;
+}
+
+int32_t tgv_run_host_stream(const tgv_config* cfg, int32_t count, const void* const* q_host_in,
+                            void* const* q_host_out, double dt, int32_t nsteps,
+                            int32_t diag_every, double* diag_host, void* dev_workspace,
+                            size_t ws_bytes, void* compute_stream, void* copy_stream) {
+  int32_t s = check(cfg);
+  if (s != TGV_OK) return s;
+  if (count < 0 || (count > 0 && (!q_host_in || !q_host_out)) || nsteps < 0 || diag_every < 0)
+    return TGV_ERR_ARG;
+  for (int32_t i = 0; i < count; ++i)
+    if (!q_host_in[i] || !q_host_out[i]) return TGV_ERR_ARG;
+  if (!dev_workspace || ws_bytes < tgv_run_host_stream_workspace_bytes(cfg, nsteps, diag_every))
+    return TGV_ERR_WORKSPACE;
+  if (count == 0) return TGV_OK;
+  const size_t qb = tgv_state_bytes(cfg), qtb = tgv_qt_bytes(cfg), wsb = tgv_workspace_bytes(cfg);
+  const size_t one = up256(tgv_run_host_workspace_bytes(cfg, nsteps, diag_every));
+  const int nrec = diag_every > 0 ? nsteps / diag_every + 1 : 0;
+  const size_t rec_bytes = (size_t)nrec * TGV_DIAG_COUNT * sizeof(double);
+  struct Set { void *qa, *qb, *qt, *dws; double* diag; } set[2];
+  for (int b = 0; b < 2; ++b) {
+    char* w = static_cast<char*>(dev_workspace) + b * one;
+    set[b] = {w, w + up256(qb), w + 2 * up256(qb), w + 2 * up256(qb) + up256(qtb),
+              reinterpret_cast<double*>(w + 2 * up256(qb) + up256(qtb) + up256(wsb))};
+  }
+  cudaStream_t cs = (cudaStream_t)compute_stream, xs = (cudaStream_t)copy_stream;
+  cudaEvent_t in_done[2] = {nullptr, nullptr}, out_ready[2] = {nullptr, nullptr};
+  std::vector<int32_t> parity((size_t)count, 0);
+  auto cleanup = [&](int32_t status) {
+    cudaStreamSynchronize(cs);
+    cudaStreamSynchronize(xs);
+    for (int b = 0; b < 2; ++b) {
+      if (in_done[b]) cudaEventDestroy(in_done[b]);
+      if (out_ready[b]) cudaEventDestroy(out_ready[b]);
+    }
+    return status;
+  };
+  for (int b = 0; b < 2; ++b)
+    if (cudaEventCreateWithFlags(&in_done[b], cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&out_ready[b], cudaEventDisableTiming) != cudaSuccess)
+      return cleanup(TGV_ERR_CUDA);
+  // copy-out of state j (issued after the copy-in of state j + 1, so that a
+  // copy-in never waits behind a copy-out that waits for the computation)
+  auto copy_out = [&](int32_t j) -> int32_t {
+    const Set& S = set[j & 1];
+    if (cudaStreamWaitEvent(xs, out_ready[j & 1], 0) != cudaSuccess) return TGV_ERR_CUDA;
+    if (cudaMemcpyAsync(q_host_out[j], parity[j] ? S.qb : S.qa, qb, cudaMemcpyDeviceToHost,
+                        xs) != cudaSuccess)
+      return TGV_ERR_CUDA;
+    if (nrec > 0 && diag_host &&
+        cudaMemcpyAsync(diag_host + (size_t)j * nrec * TGV_DIAG_COUNT, S.diag, rec_bytes,
+                        cudaMemcpyDeviceToHost, xs) != cudaSuccess)
+      return TGV_ERR_CUDA;
+    return TGV_OK;
+  };
+  for (int32_t i = 0; i < count; ++i) {
+    const Set& S = set[i & 1];
+    // set i&1 is free: the copy-out of state i-2 precedes this copy-in on xs
+    if (cudaMemcpyAsync(S.qa, q_host_in[i], qb, cudaMemcpyHostToDevice, xs) != cudaSuccess ||
+        cudaEventRecord(in_done[i & 1], xs) != cudaSuccess ||
+        cudaStreamWaitEvent(cs, in_done[i & 1], 0) != cudaSuccess)
+      return cleanup(TGV_ERR_CUDA);
+    s = rk_step(cfg, S.qa, S.qb, S.qt, dt, nsteps, diag_every, nrec > 0 ? S.diag : nullptr, S.dws,
+                wsb, &parity[i], cs);
+    if (s != TGV_OK) return cleanup(s);
+    if (cudaEventRecord(out_ready[i & 1], cs) != cudaSuccess) return cleanup(TGV_ERR_CUDA);
+    if (i > 0 && (s = copy_out(i - 1)) != TGV_OK) return cleanup(s);
+  }
+  if ((s = copy_out(count - 1)) != TGV_OK) return cleanup(s);
+  return cleanup(TGV_OK);
 }
 
 }  // extern "C"

@@ -29,6 +29,52 @@ def test_run_host_matches_device_path_bitwise(mode):
     assert torch.equal(d_host.view(3, -1), diag.cpu())
 
 
+@pytest.mark.parametrize("mode", ["fp32", "fp16_fp32"])
+@pytest.mark.parametrize("count", [1, 2, 5])
+def test_run_host_stream_matches_single_calls_bitwise(mode, count):
+    """The pipelined host call: each of `count` different states (the TGV
+    field scaled by a different factor) comes back exactly as from
+    tgv_run_host, records included, with the copies on a second stream."""
+    cfg = tgv.Config(n=32, mode=mode, encoding="offset" if mode == "fp16_fp32" else "plain")
+    q0 = tgv.empty_state(cfg)
+    tgv.tgv_init(cfg, q0)
+    base = q0.cpu()
+    ins = []
+    for i in range(count):
+        q = base.clone()
+        q[1:4] = (q[1:4].float() * (1.0 - 0.1 * i)).to(q.dtype)  # slower vortices
+        ins.append(q.pin_memory())
+    outs = [torch.empty_like(q).pin_memory() for q in ins]
+    nsteps, every = 6, 3
+    nrec = nsteps // every + 1
+    d_host = torch.zeros(count * nrec * tgv.TGV_DIAG_COUNT, dtype=torch.float64).pin_memory()
+    ws = torch.empty(tgv.tgv_run_host_stream_workspace_bytes(cfg, nsteps, every),
+                     dtype=torch.uint8, device="cuda")
+    tgv.tgv_run_host_stream(cfg, ins, outs, 0.004, nsteps, every, d_host, ws,
+                            copy_stream=torch.cuda.Stream())
+    ws1 = torch.empty(tgv.tgv_run_host_workspace_bytes(cfg, nsteps, every), dtype=torch.uint8,
+                      device="cuda")
+    for i in range(count):
+        ref = torch.empty_like(ins[i]).pin_memory()
+        d1 = torch.empty(nrec * tgv.TGV_DIAG_COUNT, dtype=torch.float64).pin_memory()
+        tgv.tgv_run_host(cfg, ins[i], ref, 0.004, nsteps, every, d1, ws1)
+        assert torch.equal(outs[i], ref), i
+        assert torch.equal(d_host.view(count, -1)[i], d1), i
+
+
+def test_run_host_stream_argument_errors():
+    cfg = tgv.Config(n=32)
+    h = torch.empty((5, 32, 32, 32), dtype=torch.float64).pin_memory()
+    small = torch.empty(8, dtype=torch.uint8, device="cuda")
+    with pytest.raises(tgv.TGVError) as ei:
+        tgv.tgv_run_host_stream(cfg, [h], [h], 0.004, 2, 0, None, small,
+                                copy_stream=torch.cuda.Stream())
+    assert ei.value.status == _abi.TGV_ERR_WORKSPACE
+    ws = torch.empty(tgv.tgv_run_host_stream_workspace_bytes(cfg, 2, 0), dtype=torch.uint8,
+                     device="cuda")
+    tgv.tgv_run_host_stream(cfg, [], [], 0.004, 2, 0, None, ws, copy_stream=torch.cuda.Stream())
+
+
 def test_workspace_errors():
     cfg = tgv.Config(n=32)
     q = tgv.empty_state(cfg)
