@@ -281,6 +281,27 @@ def profile_traffic(mode, n):
         return None
 
 
+def profile_instr_per_point(mode, n):
+    """Mean thread instructions per grid point and stage launch from the committed
+    ncu summary (if the stage kernel source is unchanged since the capture)."""
+    path = os.path.join(ROOT, "profiles", f"stage_kernel_{mode}_{n}.md")
+    try:
+        text = open(path).read()
+    except OSError:
+        return None
+    if profile_traffic(mode, n) is None:  # stale or missing capture
+        return None
+    for line in text.splitlines():
+        if line.startswith("| thread instructions per grid point"):
+            cells = [c.strip() for c in line.strip().strip("|").split("|")[1:]]
+            try:
+                vals = [float(c) for c in cells if c]
+                return sum(vals) / len(vals)
+            except ValueError:
+                return None
+    return None
+
+
 def reduce_max(v: float, dist, device) -> float:
     """Max of a per-rank scalar over all ranks (the timing rule: the slowest
     rank's time); identity without a process group."""
@@ -379,6 +400,19 @@ def run_ours(args, rank, world, local):
                 "traffic": profile_traffic(HEADLINE, n), "peak_kind": f"{peak_kind} hbm_gbs",
                 "kernel": "stage_kernel (fused RHS + RK stage)", "stage_ms": round(stage_ms, 4),
                 "alg_bytes_per_launch": alg_bytes_launch}
+    # the ceiling the FP16-storage stage actually meets: instruction issue (148 SMs x
+    # 4 schedulers x one warp instruction of 32 threads per clock at 2032 MHz)
+    ipp = profile_instr_per_point(HEADLINE, n)
+    issue_roof = None
+    if ipp is not None:
+        peak_issue = 148 * 4 * 32 * 2.032e9 / 1e9
+        ach_issue = ipp * n ** 3 / (stage_ms * 1e-3) / 1e9
+        issue_roof = {"bound": "issue", "achieved": round(ach_issue, 1), "peak": round(peak_issue, 1),
+                      "unit": "G thread-instructions/s", "frac": round(ach_issue / peak_issue, 4),
+                      "instr_per_point": round(ipp, 1),
+                      "source": "thread instructions per point from the committed ncu summary, "
+                                "time from this run; peak from the unit counts at the maximum "
+                                "SM clock"}
     del qa, qb, qt
     torch.cuda.empty_cache()
 
@@ -463,7 +497,8 @@ def run_ours(args, rank, world, local):
     if dist is not None:
         dist.destroy_process_group()
     return {
-        "value": value, "ms_per_step": ms_step, "roofline": roofline, "e2e": e2e,
+        "value": value, "ms_per_step": ms_step, "roofline": roofline,
+        "roofline_issue": issue_roof, "e2e": e2e,
         "gpu_launches": launches, "clocks": clk.summary(), "modes": modes,
         "diag_last": dict(zip(tgv.DIAG_NAMES, diag_last)), "dt": dt, **extra,
     }
@@ -685,8 +720,8 @@ def main():
     if rank != 0:
         return
     line = dict(base, value=res["value"], ms_per_step=res["ms_per_step"], dtype="f32",
-                config=config, roofline=res["roofline"], e2e=res["e2e"],
-                gpu_launches=res["gpu_launches"], clocks=res["clocks"], modes=res["modes"],
+                config=config, roofline=res["roofline"], roofline_issue=res["roofline_issue"],
+                e2e=res["e2e"], gpu_launches=res["gpu_launches"], clocks=res["clocks"], modes=res["modes"],
                 diag_last=res["diag_last"])
     for key in ("n512", "tgsym_256", "graph_32", "adjoint_64", "ensemble_48"):
         if key in res:
