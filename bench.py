@@ -21,6 +21,7 @@ import hashlib
 import json
 import math
 import os
+import re
 import statistics
 import subprocess
 import sys
@@ -259,6 +260,16 @@ def measured_peaks():
         return {"hbm_gbs": 6400.0, "bf16_tflops": 1800.0}, "fallback"
 
 
+def stage_source_sha():
+    """First 16 hex digits of the SHA-256 of the stage kernel's source with its
+    comments and blank lines removed (a comment edit keeps a capture valid)."""
+    src = open(STAGE_SRC).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    src = re.sub(r"//[^\n]*", "", src)
+    code = "\n".join(line.rstrip() for line in src.splitlines() if line.strip())
+    return hashlib.sha256(code.encode()).hexdigest()[:16]
+
+
 def profile_traffic(mode, n):
     """dram read+write bytes per stage launch from the committed ncu summary,
     if the stage kernel source is unchanged since the capture; else None."""
@@ -267,7 +278,7 @@ def profile_traffic(mode, n):
         text = open(path).read()
     except OSError:
         return None
-    sha = hashlib.sha256(open(STAGE_SRC, "rb").read()).hexdigest()[:16]
+    sha = stage_source_sha()
     vals = {}
     for line in text.splitlines():
         if ":" in line and line.strip().startswith("- "):

@@ -1,17 +1,20 @@
 // tgv_stage.cuh - the fused RHS + low-storage-RK stage kernel.
 //
 // One launch evaluates the residual R(Q) of the compressible Navier-Stokes
-// equations (4th-order central differences, Blaisdell split convective terms,
+// equations (4th-order central differences, split convective terms,
 // Sec. 2.3.1) at every grid point and folds the RK update of Sec. 3.1,
-// Eqs. 3-4, into its epilogue:  Qt <- A Qt + dt R,  Q_out <- Q_in + B Qt.
+// Eqs. 3-4, into its epilogue:  Qt <- A Qt + dt R,  Q_out <- Q_in + B Qt
+// (rk_step keeps W = Qt/dt instead: W <- A W + R, Q_out <- Q_in + (B dt) W).
 // With EPI_RHS it writes R instead.  With DIAG it also reduces the
 // diagnostics of Sec. 4.1, Eqs. 11-12 of its input state.
 //
 // Discrete operator (identical to the FP64 oracle's, up to rounding order):
 //   D f  = (-f[+2] + 8 f[+1] - 8 f[-1] + f[-2]) / 12h
 //   D2 f = (-f[+2] + 16 f[+1] - 30 f[0] + 16 f[-1] - f[-2]) / 12h^2
-//   C_c  = a sum_j D_j(u_j f_c) + b [sum_j u_j D_j f_c + f_c div u]
-//          (Blaisdell: a = b = 1/2;  divergence form: a = 1, b = 0)
+//   C_c  = a sum_j D_j(u_j f_c) + b [sum_j u_j D_j f_c + f_c div u] (+ g kx_c)
+//          (Blaisdell: a = b = 1/2;  divergence form: a = 1, b = 0; the
+//          KGP, KEEP and Feiereisen variants add the terms kx of kgp_extra
+//          and keep_extra)
 //   R_rho   = -C_rho
 //   R_m(i)  = -C_m(i) - D_i p + nu [sum_j (1 + delta_ij/3) D2_j u_i + 1/3 D_i s_i]
 //   R_E     = -C_E - sum_j D_j(p u_j) + sum_j D2_j H_j
@@ -28,13 +31,15 @@
 // is read once from HBM (periodic wrap, or mirror images in the symmetric
 // box; the next plane is staged into shared memory by cp.async while the
 // current one is computed), converted to the compute type, and turned into
-// primitives in a 5-plane shared-memory ring.  Per
-// plane, with two CTA barriers:
+// primitives in a 5-plane shared-memory ring.  Per plane, with two CTA
+// barriers:
 //   1. primitives of the prefetched plane zl -> ring slot            | barrier
-//   2. prefetch plane zl+1; D_x u + D_y v of plane zl (z-taps of s_z);
-//      centre plane k = zl-2: s_x, s_y and the mixed-derivative fields on
-//      the tile and its x/y halo strips (double-buffered)              | barrier
-//   3. every term at plane k for the thread's unit, RK epilogue.
+//   2. prefetch plane zl+1 (and the next centre plane's Qt); D_x u + D_y v
+//      of plane zl (z-taps of s_z); centre plane k = zl-2: s_x, s_y and the
+//      mixed-derivative fields on the tile and its x/y halo strips, and
+//      every z-direction term of the thread's unit                   | barrier
+//   3. the x- and y-direction terms at plane k (centre plane and strips
+//      only), assembly of R, RK epilogue.
 #pragma once
 
 #include "tgv_common.cuh"
