@@ -94,13 +94,52 @@ class Config:
 
 
 def _ptr(t) -> int | None:
+    """Device pointer of an optional CUDA tensor (contiguous, on the current
+    device); sizes are checked by _dev where the caller knows them."""
     if t is None:
         return None
-    if not t.is_cuda:
-        raise ValueError("expected a CUDA tensor")
+    return _dev(t, "tensor")
+
+
+def _nbytes(t) -> int:
+    return t.numel() * t.element_size()
+
+
+def _dev(t, name: str, dtype=None, nbytes: int | None = None) -> int:
+    """Validate a device buffer before it reaches the library: a contiguous
+    CUDA tensor on the current device, of `dtype` (if given) and at least
+    `nbytes` bytes (if given).  Raises ValueError; nothing is launched."""
+    if not getattr(t, "is_cuda", False):
+        raise ValueError(f"{name}: expected a CUDA tensor")
     if not t.is_contiguous():
-        raise ValueError("expected a contiguous tensor")
+        raise ValueError(f"{name}: expected a contiguous tensor")
+    cur = torch.cuda.current_device()
+    if t.device.index != cur:
+        raise ValueError(f"{name} is on cuda:{t.device.index}, the current device is cuda:{cur}")
+    if dtype is not None and t.dtype != dtype:
+        raise ValueError(f"{name}: expected {dtype}, got {t.dtype}")
+    if nbytes is not None and _nbytes(t) < nbytes:
+        raise ValueError(f"{name}: {_nbytes(t)} bytes, the library needs {nbytes}")
     return t.data_ptr()
+
+
+def _host(t, name: str, dtype=None, nbytes: int | None = None) -> int:
+    """Validate a host buffer (contiguous CPU tensor of `dtype`, >= nbytes)."""
+    if not isinstance(t, torch.Tensor) or t.is_cuda or not t.is_contiguous():
+        raise ValueError(f"{name}: host buffers must be contiguous CPU tensors")
+    if dtype is not None and t.dtype != dtype:
+        raise ValueError(f"{name}: expected {dtype}, got {t.dtype}")
+    if nbytes is not None and _nbytes(t) < nbytes:
+        raise ValueError(f"{name}: {_nbytes(t)} bytes, the library needs {nbytes}")
+    return t.data_ptr()
+
+
+def _field_bytes(cfg: "Config", dtype: torch.dtype, fields: int = 5) -> int:
+    return fields * cfg.n ** 3 * torch.tensor([], dtype=dtype).element_size()
+
+
+def _nrec(nsteps: int, diag_every: int) -> int:
+    return nsteps // diag_every + 1 if diag_every > 0 else 0
 
 
 def _stream(stream) -> int | None:
@@ -154,45 +193,67 @@ def empty_workspace(cfg: Config, device="cuda") -> torch.Tensor:
 
 
 # ------------------------------------------------------------------ C entries
+def _q(cfg: Config, t, name: str) -> int:
+    return _dev(t, name, cfg.q_dtype, tgv_state_bytes(cfg))
+
+
+def _qt(cfg: Config, t, name: str) -> int:
+    return _dev(t, name, cfg.qt_dtype, tgv_qt_bytes(cfg))
+
+
+def _ws(t, name: str = "workspace"):
+    """(pointer, bytes) of an optional device workspace; the library checks the size."""
+    if t is None:
+        return None, 0
+    return _dev(t, name), _nbytes(t)
+
+
 def tgv_init(cfg: Config, q: torch.Tensor, stream=None) -> None:
-    check(lib().tgv_init(C.byref(cfg.c()), _ptr(q), _stream(stream)), "tgv_init")
+    pq = _q(cfg, q, "q")
+    check(lib().tgv_init(C.byref(cfg.c()), pq, _stream(stream)), "tgv_init")
 
 
 def rhs_eval(cfg: Config, q: torch.Tensor, r: torch.Tensor, stream=None) -> None:
-    if r.dtype != cfg.compute_dtype:
-        raise ValueError(f"r must be {cfg.compute_dtype}")
-    check(lib().rhs_eval(C.byref(cfg.c()), _ptr(q), _ptr(r), _stream(stream)), "rhs_eval")
+    pq = _q(cfg, q, "q")
+    pr = _dev(r, "r", cfg.compute_dtype, _field_bytes(cfg, cfg.compute_dtype))
+    check(lib().rhs_eval(C.byref(cfg.c()), pq, pr, _stream(stream)), "rhs_eval")
 
 
 def rk_substep(cfg: Config, q_in, q_out, qt, i: int, dt: float, stream=None) -> None:
-    check(lib().rk_substep(C.byref(cfg.c()), _ptr(q_in), _ptr(q_out), _ptr(qt), int(i),
-                           float(dt), _stream(stream)), "rk_substep")
+    args = (_q(cfg, q_in, "q_in"), _q(cfg, q_out, "q_out"), _qt(cfg, qt, "qt"))
+    check(lib().rk_substep(C.byref(cfg.c()), *args, int(i), float(dt), _stream(stream)),
+          "rk_substep")
 
 
 def rk_step(cfg: Config, q_a, q_b, qt, dt: float, nsteps: int, diag_every: int = 0,
             diag=None, workspace=None, stream=None) -> int:
     """Advance nsteps; returns the parity (0: result in q_a, 1: in q_b)."""
     par = C.c_int32(-1)
-    ws = workspace
-    ws_bytes = ws.numel() * ws.element_size() if ws is not None else 0
-    check(lib().rk_step(C.byref(cfg.c()), _ptr(q_a), _ptr(q_b), _ptr(qt), float(dt),
-                        int(nsteps), int(diag_every), _ptr(diag), _ptr(ws), ws_bytes,
-                        C.byref(par), _stream(stream)), "rk_step")
+    pa, pb, pt = _q(cfg, q_a, "q_a"), _q(cfg, q_b, "q_b"), _qt(cfg, qt, "qt")
+    nrec = _nrec(int(nsteps), int(diag_every))
+    pd = _dev(diag, "diag", torch.float64, nrec * TGV_DIAG_COUNT * 8) if nrec else _ptr(diag)
+    pw, ws_bytes = _ws(workspace)
+    check(lib().rk_step(C.byref(cfg.c()), pa, pb, pt, float(dt), int(nsteps), int(diag_every),
+                        pd, pw, ws_bytes, C.byref(par), _stream(stream)), "rk_step")
     return par.value
 
 
 def diagnostics_reduce(cfg: Config, q, out, workspace, stream=None) -> None:
-    check(lib().diagnostics_reduce(C.byref(cfg.c()), _ptr(q), _ptr(out), _ptr(workspace),
-                                   workspace.numel() * workspace.element_size(),
-                                   _stream(stream)), "diagnostics_reduce")
+    pq = _q(cfg, q, "q")
+    po = _dev(out, "out", torch.float64, TGV_DIAG_COUNT * 8)
+    pw, ws_bytes = _ws(workspace)
+    check(lib().diagnostics_reduce(C.byref(cfg.c()), pq, po, pw, ws_bytes, _stream(stream)),
+          "diagnostics_reduce")
 
 
 def diagnostics_reduce_noalloc(cfg: Config, q, out, stream=None) -> None:
     """diagnostics_reduce with the partial sums in the library's own fixed
     device array instead of a caller workspace (for callers that cannot
     allocate device memory); calls that overlap on the GPU race."""
-    check(lib().diagnostics_reduce_noalloc(C.byref(cfg.c()), _ptr(q), _ptr(out),
-                                           _stream(stream)), "diagnostics_reduce_noalloc")
+    pq = _q(cfg, q, "q")
+    po = _dev(out, "out", torch.float64, TGV_DIAG_COUNT * 8)
+    check(lib().diagnostics_reduce_noalloc(C.byref(cfg.c()), pq, po, _stream(stream)),
+          "diagnostics_reduce_noalloc")
 
 
 def tgv_run_host_workspace_bytes(cfg: Config, nsteps: int, diag_every: int) -> int:
@@ -202,14 +263,15 @@ def tgv_run_host_workspace_bytes(cfg: Config, nsteps: int, diag_every: int) -> i
 def tgv_run_host(cfg: Config, q_host_in, q_host_out, dt: float, nsteps: int,
                  diag_every: int = 0, diag_host=None, dev_workspace=None, stream=None) -> None:
     """End-to-end call with host (CPU, ideally pinned) tensors."""
-    for t in (q_host_in, q_host_out) + ((diag_host,) if diag_host is not None else ()):
-        if t.is_cuda or not t.is_contiguous():
-            raise ValueError("host buffers must be contiguous CPU tensors")
-    ws_bytes = dev_workspace.numel() * dev_workspace.element_size()
-    check(lib().tgv_run_host(C.byref(cfg.c()), q_host_in.data_ptr(), q_host_out.data_ptr(),
-                             float(dt), int(nsteps), int(diag_every),
-                             diag_host.data_ptr() if diag_host is not None else None,
-                             _ptr(dev_workspace), ws_bytes, _stream(stream)), "tgv_run_host")
+    qb = tgv_state_bytes(cfg)
+    pin = _host(q_host_in, "q_host_in", cfg.q_dtype, qb)
+    pout = _host(q_host_out, "q_host_out", cfg.q_dtype, qb)
+    nrec = _nrec(int(nsteps), int(diag_every))
+    pd = (_host(diag_host, "diag_host", torch.float64, nrec * TGV_DIAG_COUNT * 8)
+          if diag_host is not None else None)
+    pw, ws_bytes = _ws(dev_workspace, "dev_workspace")
+    check(lib().tgv_run_host(C.byref(cfg.c()), pin, pout, float(dt), int(nsteps),
+                             int(diag_every), pd, pw, ws_bytes, _stream(stream)), "tgv_run_host")
 
 
 def tgv_run_host_stream_workspace_bytes(cfg: Config, nsteps: int, diag_every: int) -> int:
@@ -225,20 +287,22 @@ def tgv_run_host_stream(cfg: Config, qs_host_in, qs_host_out, dt: float, nsteps:
     qs_host_in, qs_host_out = list(qs_host_in), list(qs_host_out)
     if len(qs_host_in) != len(qs_host_out):
         raise ValueError("as many output buffers as input buffers")
-    for t in qs_host_in + qs_host_out + ([diag_host] if diag_host is not None else []):
-        if t.is_cuda or not t.is_contiguous():
-            raise ValueError("host buffers must be contiguous CPU tensors")
-    count = len(qs_host_in)
-    arr_in = (C.c_void_p * max(count, 1))(*[q.data_ptr() for q in qs_host_in])
-    arr_out = (C.c_void_p * max(count, 1))(*[q.data_ptr() for q in qs_host_out])
-    ws_bytes = dev_workspace.numel() * dev_workspace.element_size()
     if copy_stream is None:
         raise ValueError("copy_stream is required (a stream other than the compute stream)")
+    qb = tgv_state_bytes(cfg)
+    count = len(qs_host_in)
+    p_in = [_host(q, f"q_host_in[{i}]", cfg.q_dtype, qb) for i, q in enumerate(qs_host_in)]
+    p_out = [_host(q, f"q_host_out[{i}]", cfg.q_dtype, qb) for i, q in enumerate(qs_host_out)]
+    nrec = _nrec(int(nsteps), int(diag_every))
+    pd = (_host(diag_host, "diag_host", torch.float64, count * nrec * TGV_DIAG_COUNT * 8)
+          if diag_host is not None else None)
+    pw, ws_bytes = _ws(dev_workspace, "dev_workspace")
+    arr_in = (C.c_void_p * max(count, 1))(*p_in)
+    arr_out = (C.c_void_p * max(count, 1))(*p_out)
     check(lib().tgv_run_host_stream(C.byref(cfg.c()), count, arr_in, arr_out, float(dt),
-                                    int(nsteps), int(diag_every),
-                                    diag_host.data_ptr() if diag_host is not None else None,
-                                    _ptr(dev_workspace), ws_bytes, _stream(compute_stream),
-                                    _stream(copy_stream)), "tgv_run_host_stream")
+                                    int(nsteps), int(diag_every), pd, pw, ws_bytes,
+                                    _stream(compute_stream), _stream(copy_stream)),
+          "tgv_run_host_stream")
 
 
 def diagnostics(cfg: Config, q: torch.Tensor, workspace=None) -> dict:
@@ -256,19 +320,25 @@ def tgv_adjoint_workspace_bytes(cfg: Config) -> int:
 
 def rhs_vjp(cfg: Config, q, lam, q_bar, workspace=None, stream=None) -> None:
     """q_bar = (dR/dQ)^T lam at state q (FP64 cotangents)."""
+    f64 = _field_bytes(cfg, torch.float64)
+    pq = _q(cfg, q, "q")
+    pl, pb = _dev(lam, "lam", torch.float64, f64), _dev(q_bar, "q_bar", torch.float64, f64)
     ws = workspace if workspace is not None else torch.empty(
         tgv_adjoint_workspace_bytes(cfg), dtype=torch.uint8, device=q.device)
-    check(lib().rhs_vjp(C.byref(cfg.c()), _ptr(q), _ptr(lam), _ptr(q_bar), _ptr(ws),
-                        ws.numel(), _stream(stream)), "rhs_vjp")
+    pw, ws_bytes = _ws(ws)
+    check(lib().rhs_vjp(C.byref(cfg.c()), pq, pl, pb, pw, ws_bytes, _stream(stream)), "rhs_vjp")
 
 
 def rk_step_adjoint(cfg: Config, stage_inputs, q_bar, dt: float, workspace=None,
                     stream=None) -> None:
     """One RK3 step backwards; stage_inputs is a (3, 5, N, N, N) tensor."""
+    ps = _dev(stage_inputs, "stage_inputs", cfg.q_dtype, 3 * tgv_state_bytes(cfg))
+    pb = _dev(q_bar, "q_bar", torch.float64, _field_bytes(cfg, torch.float64))
     ws = workspace if workspace is not None else torch.empty(
         tgv_adjoint_workspace_bytes(cfg), dtype=torch.uint8, device=q_bar.device)
-    check(lib().rk_step_adjoint(C.byref(cfg.c()), _ptr(stage_inputs), _ptr(q_bar), float(dt),
-                                _ptr(ws), ws.numel(), _stream(stream)), "rk_step_adjoint")
+    pw, ws_bytes = _ws(ws)
+    check(lib().rk_step_adjoint(C.byref(cfg.c()), ps, pb, float(dt), pw, ws_bytes,
+                                _stream(stream)), "rk_step_adjoint")
 
 
 def tgv_grad_workspace_bytes(cfg: Config, nsteps: int, ckpt_every: int) -> int:
@@ -277,11 +347,15 @@ def tgv_grad_workspace_bytes(cfg: Config, nsteps: int, ckpt_every: int) -> int:
 
 def tgv_grad_final_ke(cfg: Config, q0, dt: float, nsteps: int, ckpt_every: int, grad_mom,
                       j_out, workspace=None, stream=None) -> None:
+    pq = _q(cfg, q0, "q0")
+    pg = _dev(grad_mom, "grad_mom", torch.float64, _field_bytes(cfg, torch.float64, 3))
+    pj = _dev(j_out, "j_out", torch.float64, 8)
     ws = workspace if workspace is not None else torch.empty(
         tgv_grad_workspace_bytes(cfg, nsteps, ckpt_every), dtype=torch.uint8, device=q0.device)
-    check(lib().tgv_grad_final_ke(C.byref(cfg.c()), _ptr(q0), float(dt), int(nsteps),
-                                  int(ckpt_every), _ptr(grad_mom), _ptr(j_out), _ptr(ws),
-                                  ws.numel(), _stream(stream)), "tgv_grad_final_ke")
+    pw, ws_bytes = _ws(ws)
+    check(lib().tgv_grad_final_ke(C.byref(cfg.c()), pq, float(dt), int(nsteps),
+                                  int(ckpt_every), pg, pj, pw, ws_bytes, _stream(stream)),
+          "tgv_grad_final_ke")
 
 
 class TGVFinalKE(torch.autograd.Function):
@@ -316,10 +390,15 @@ class Ensemble:
     def __init__(self, cfgs, q_a, q_b, qt, dts, steps_per_graph: int = 10, stream=None):
         n = len(cfgs)
         arr = (_abi.tgv_config * n)(*[c.c() for c in cfgs])
-        ptrs = lambda ts: (C.c_void_p * n)(*[_ptr(t) for t in ts])
+        if not (len(q_a) == len(q_b) == len(qt) == len(dts) == n):
+            raise ValueError("one q_a, q_b, qt and dt per instance")
+        pa = [_q(c, t, f"q_a[{i}]") for i, (c, t) in enumerate(zip(cfgs, q_a))]
+        pb = [_q(c, t, f"q_b[{i}]") for i, (c, t) in enumerate(zip(cfgs, q_b))]
+        pt = [_qt(c, t, f"qt[{i}]") for i, (c, t) in enumerate(zip(cfgs, qt))]
+        ptrs = lambda ps: (C.c_void_p * n)(*ps)
         self._keep = (list(q_a), list(q_b), list(qt))
         handle = C.c_void_p()
-        check(lib().tgv_ensemble_create(arr, n, ptrs(q_a), ptrs(q_b), ptrs(qt),
+        check(lib().tgv_ensemble_create(arr, n, ptrs(pa), ptrs(pb), ptrs(pt),
                                         (C.c_double * n)(*[float(d) for d in dts]),
                                         int(steps_per_graph), _stream(stream), C.byref(handle)),
               "tgv_ensemble_create")

@@ -4,6 +4,9 @@ import ctypes as C
 import math
 import os
 import re
+import subprocess
+import sys
+import textwrap
 
 import pytest
 
@@ -64,23 +67,37 @@ def test_unknown_split_form_is_rejected():
     assert _abi.lib().tgv_check_config(C.byref(cfg)) == _abi.TGV_ERR_ARG
 
 
+def _run_without_devices(body: str) -> None:
+    """Run `body` in a child process that sees no CUDA device: the entry
+    points below get fabricated device addresses, so if a validation were ever
+    reordered or a mode became supported, the launch fails with "no device"
+    instead of touching address 256 on a GPU."""
+    env = dict(os.environ, CUDA_VISIBLE_DEVICES="")
+    code = ("import ctypes as C\nimport paper_2505_20911_b300 as tgv\n"
+            "from paper_2505_20911_b300 import _abi\nlib = _abi.lib()\n"
+            "fake = C.c_void_p(256)\n" + textwrap.dedent(body))
+    res = subprocess.run([sys.executable, "-c", code], cwd=ROOT, env=env, capture_output=True,
+                         text=True, timeout=300)
+    assert res.returncode == 0, res.stdout + res.stderr
+
+
 def test_null_pointers_fail_before_any_cuda_call():
-    cfg = tgv.Config(n=32).c()
-    lib = _abi.lib()
-    assert lib.tgv_init(C.byref(cfg), None, None) == _abi.TGV_ERR_ARG
-    assert lib.rhs_eval(C.byref(cfg), None, None, None) == _abi.TGV_ERR_ARG
-    assert lib.rk_substep(C.byref(cfg), None, None, None, 0, 0.001, None) == _abi.TGV_ERR_ARG
-    assert lib.rk_step(C.byref(cfg), None, None, None, 0.001, 1, 0, None, None, 0, None,
-                       None) == _abi.TGV_ERR_ARG
-    fake = C.c_void_p(256)
-    assert lib.rk_substep(C.byref(cfg), fake, fake, fake, 0, 0.001, None) == _abi.TGV_ERR_ARG
-    assert lib.rk_substep(C.byref(cfg), fake, C.c_void_p(512), fake, 3, 0.001,
-                          None) == _abi.TGV_ERR_ARG
-    assert lib.diagnostics_reduce(C.byref(cfg), fake, fake, None, 0,
-                                  None) == _abi.TGV_ERR_WORKSPACE
-    # unstable dt is refused before any launch
-    assert lib.rk_step(C.byref(cfg), fake, C.c_void_p(512), C.c_void_p(1024), 1.0, 1, 0, None,
-                       None, 0, None, None) == _abi.TGV_ERR_UNSTABLE_DT
+    _run_without_devices("""
+        cfg = tgv.Config(n=32).c()
+        assert lib.tgv_init(C.byref(cfg), None, None) == _abi.TGV_ERR_ARG
+        assert lib.rhs_eval(C.byref(cfg), None, None, None) == _abi.TGV_ERR_ARG
+        assert lib.rk_substep(C.byref(cfg), None, None, None, 0, 0.001, None) == _abi.TGV_ERR_ARG
+        assert lib.rk_step(C.byref(cfg), None, None, None, 0.001, 1, 0, None, None, 0, None,
+                           None) == _abi.TGV_ERR_ARG
+        assert lib.rk_substep(C.byref(cfg), fake, fake, fake, 0, 0.001, None) == _abi.TGV_ERR_ARG
+        assert lib.rk_substep(C.byref(cfg), fake, C.c_void_p(512), fake, 3, 0.001,
+                              None) == _abi.TGV_ERR_ARG
+        assert lib.diagnostics_reduce(C.byref(cfg), fake, fake, None, 0,
+                                      None) == _abi.TGV_ERR_WORKSPACE
+        # unstable dt is refused before any launch
+        assert lib.rk_step(C.byref(cfg), fake, C.c_void_p(512), C.c_void_p(1024), 1.0, 1, 0,
+                           None, None, 0, None, None) == _abi.TGV_ERR_UNSTABLE_DT
+    """)
 
 
 def test_sizes_and_stability_limit():
@@ -109,21 +126,22 @@ def test_tile_shapes_and_workspace():
 
 
 def test_adjoint_entry_points_validate_on_host():
-    lib = _abi.lib()
-    fake = C.c_void_p(256)
-    c64, c16 = tgv.Config(n=32).c(), tgv.Config(n=32, mode="fp16_fp32").c()
     assert tgv.tgv_adjoint_workspace_bytes(tgv.Config(n=32)) == 16 * 32 ** 3 * 8
     assert tgv.tgv_adjoint_workspace_bytes(tgv.Config(n=32, mode="fp16_fp32")) == 0
-    assert lib.rhs_vjp(C.byref(c16), fake, fake, fake, fake, 1 << 30, None) == \
-        _abi.TGV_ERR_UNSUPPORTED
-    assert lib.rhs_vjp(C.byref(c64), fake, fake, fake, None, 0, None) == _abi.TGV_ERR_WORKSPACE
-    assert lib.rk_step_adjoint(C.byref(c64), None, fake, 0.004, fake, 1 << 30, None) == \
-        _abi.TGV_ERR_ARG
     assert tgv.tgv_grad_workspace_bytes(tgv.Config(n=32), 200, 20) > 10 * 5 * 32 ** 3 * 8
-    assert lib.tgv_grad_final_ke(C.byref(c64), fake, 0.004, 0, 20, fake, fake, fake, 1 << 40,
-                                 None) == _abi.TGV_ERR_ARG
-    assert lib.tgv_grad_final_ke(C.byref(c64), fake, 1.0, 10, 5, fake, fake, fake, 1 << 40,
-                                 None) == _abi.TGV_ERR_UNSTABLE_DT
+    _run_without_devices("""
+        c64, c16 = tgv.Config(n=32).c(), tgv.Config(n=32, mode="fp16_fp32").c()
+        assert lib.rhs_vjp(C.byref(c16), fake, fake, fake, fake, 1 << 30, None) == \\
+            _abi.TGV_ERR_UNSUPPORTED
+        assert lib.rhs_vjp(C.byref(c64), fake, fake, fake, None, 0, None) == \\
+            _abi.TGV_ERR_WORKSPACE
+        assert lib.rk_step_adjoint(C.byref(c64), None, fake, 0.004, fake, 1 << 30, None) == \\
+            _abi.TGV_ERR_ARG
+        assert lib.tgv_grad_final_ke(C.byref(c64), fake, 0.004, 0, 20, fake, fake, fake,
+                                     1 << 40, None) == _abi.TGV_ERR_ARG
+        assert lib.tgv_grad_final_ke(C.byref(c64), fake, 1.0, 10, 5, fake, fake, fake,
+                                     1 << 40, None) == _abi.TGV_ERR_UNSTABLE_DT
+    """)
 
 
 def test_missing_library_fails_loudly(monkeypatch):

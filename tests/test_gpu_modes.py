@@ -21,7 +21,17 @@ pytestmark = pytest.mark.gpu
 
 N, DT, STEPS, EVERY = 32, 0.004, 100, 10
 
-# mode -> (encoding, bound on field errors, bound on dissipation-rate error)
+# The method's accuracy target for the reduced-precision modes: the relative
+# error of the dissipation rate -dK/dt against the FP64 oracle at most 1e-2.
+DISS_TARGET = 1e-2
+
+# mode -> (encoding, bound on field errors, bound on dissipation-rate error, kind)
+#   kind "target": the mode is offered as meeting DISS_TARGET; its bound is
+#     the tighter of DISS_TARGET and the rounding-derived bound below, and the
+#     test also asserts DISS_TARGET itself.
+#   kind "measured": the mode does not meet DISS_TARGET (Q stored in 16 bits);
+#     its bounds are a regression band of about 3x the errors measured on a
+#     B300 at this size, not the target.
 #   FP32-class arithmetic and Q storage (u = 6e-8): about STEPS * 3 roundings
 #     of Q whose effect on the momentum is amplified by the pressure-dominated
 #     flux sums (|rho E + p| / |R| ~ 1e2): fields ~1e-5, dissipation rate
@@ -30,17 +40,15 @@ N, DT, STEPS, EVERY = 32, 0.004, 100, 10
 #     the stage increments B dt R ~ 3e-4 are comparable to half an ulp, so
 #     round-to-nearest drops or biases them; the momentum drifts by 1e-2 and
 #     the dissipation rate, which lives on those increments, is not resolved.
-#     The field bound is a few ulp per 100 steps; the dissipation rate is
-#     reported, not bounded (None).
 MODES = {
-    "fp64": ("plain", 1e-10, 1e-8),
-    "spdp": ("plain", 5e-6, 1e-4),
-    "fp32s_fp64c": ("plain", 2e-5, 5e-4),
-    "fp32": ("plain", 2e-5, 5e-4),
-    "hpsp": ("plain", 2e-5, 5e-4),
-    "bf16_fp32": ("offset", 2e-1, None),
-    "fp16_fp32": ("offset", 5e-2, None),
-    "fp16": ("offset", 1e-1, None),
+    "fp64": ("plain", 1e-10, 1e-8, "target"),
+    "spdp": ("plain", 5e-6, 1e-4, "target"),
+    "fp32s_fp64c": ("plain", 2e-5, 5e-4, "target"),
+    "fp32": ("plain", 2e-5, 5e-4, "target"),
+    "hpsp": ("plain", 2e-5, 5e-4, "target"),
+    "bf16_fp32": ("offset", 2e-1, None, "measured"),
+    "fp16_fp32": ("offset", 5e-2, None, "measured"),
+    "fp16": ("offset", 1e-1, None, "measured"),
 }
 
 
@@ -85,12 +93,14 @@ def mode_errors(mode, encoding, reference):
 
 @pytest.mark.parametrize("mode", list(MODES))
 def test_mode_error_against_oracle(mode, reference):
-    enc, bound_field, bound_diss = MODES[mode]
+    enc, bound_field, bound_diss, kind = MODES[mode]
     e = mode_errors(mode, enc, reference)
-    print(f"\n{mode:12s} {enc:6s} " + " ".join(f"{k}={v:.2e}" for k, v in e.items()))
+    print(f"\n{mode:12s} {enc:6s} {kind:8s} " + " ".join(f"{k}={v:.2e}" for k, v in e.items()))
     assert all(math.isfinite(v) for v in e.values()), (mode, e)
     assert max(e["rho"], e["mom"], e["rhoE"]) <= bound_field, (mode, e)
-    if bound_diss is not None:
+    if kind == "target":
+        assert e["diss"] <= min(bound_diss, DISS_TARGET), (mode, e)
+    elif bound_diss is not None:
         assert e["diss"] <= bound_diss, (mode, e)
 
 
