@@ -14,8 +14,11 @@ every other mode of the sweep is timed in the same run and reported under
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
 
-Under torchrun (N > 1) every rank advances its own replica (weak scaling, no
-collective on the data path); value = all ranks' point-steps / max time.
+Under torchrun (N > 1) the same box is split into z-slabs, one per rank, with
+the ghost planes exchanged (NCCL point-to-point) before every RK stage
+(strong scaling); value = the box's point-steps / max time over ranks.  The
+replica figure (one independent box per rank, weak scaling) is reported
+beside it.
 """
 from __future__ import annotations
 
@@ -316,6 +319,23 @@ def profile_instr_per_point(mode, n):
     return None
 
 
+def op_tally_flops(split: str = "blaisdell"):
+    """Flops per grid point and RK stage counted from the oracle's formulas
+    (the committed summary written by tests/op_tally.py), or None."""
+    try:
+        text = open(os.path.join(ROOT, "profiles", "op_tally.md")).read()
+    except OSError:
+        return None
+    m = re.search(rf"flops_per_point_stage_{split}: `(\d+)`", text)
+    return float(m.group(1)) if m else None
+
+
+def fp32_peak_tflops(sms: int, sm_mhz: float) -> float:
+    """FP32 peak from the unit counts and clock: SMs x 128 FP32 lanes x 2 flops
+    (one fused multiply-add) per cycle at the given SM clock."""
+    return sms * 128 * 2 * sm_mhz * 1e6 / 1e12
+
+
 def reduce_max(v: float, dist, device) -> float:
     """Max of a per-rank scalar over all ranks (the timing rule: the slowest
     rank's time); identity without a process group."""
@@ -340,8 +360,10 @@ def run_ours(args, rank, world, local):
     dev = torch.device("cuda", local)
     dist = None
     if world > 1:
+        import datetime
         import torch.distributed as dist
-        dist.init_process_group("nccl", device_id=dev)
+        # a short timeout: a mismatched exchange ends in an error, not a hang
+        dist.init_process_group("nccl", device_id=dev, timeout=datetime.timedelta(seconds=120))
 
     def barrier():
         if dist is not None:
@@ -385,6 +407,20 @@ def run_ours(args, rank, world, local):
     ms = max_over_ranks(ms)
     ms_step = ms / K
     value = whole_job_value(n ** 3, K, world, ms)
+    replicas = None
+    slab_run = None
+    if world > 1:
+        # the method's parallel strategy: one n^3 box in z-slabs over the
+        # ranks (strong scaling), ghosts exchanged before every stage; the
+        # replica figure above is kept beside it
+        replicas = {"value": value, "ms_per_step": ms / K, "scaling": "weak",
+                    "what": f"one independent {n}^3 box per rank, no data-path collective"}
+        try:
+            slab_run = run_slab(tgv, torch, dist, rank, world, dev, n, dt, K, W, barrier,
+                                max_over_ranks)
+            value, ms = slab_run["value"], slab_run["ms"]
+        except Exception as exc:  # report, do not hide: the line then carries the replicas
+            slab_run = {"error": repr(exc)}
     diag_last = diag[nrec - 1].cpu().tolist()
     # 3 stage launches per step (the first of each logged step fuses the
     # diagnostics), one final-reduction launch per logged step, and the
@@ -409,11 +445,33 @@ def run_ours(args, rank, world, local):
     alg_bytes_launch = bpp / 3.0 * n ** 3
     peaks, peak_kind = measured_peaks()
     achieved = alg_bytes_launch / (stage_ms * 1e-3) / 1e9
+    traffic = profile_traffic(HEADLINE, n)
     roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peaks["hbm_gbs"],
                 "unit": "GB/s", "frac": round(achieved / peaks["hbm_gbs"], 4),
-                "traffic": profile_traffic(HEADLINE, n), "peak_kind": f"{peak_kind} hbm_gbs",
+                "traffic": traffic,
+                "traffic_note": (f"ncu dram read+write per launch from profiles/stage_kernel_"
+                                 f"{HEADLINE}_{n}.md, captured on this stage kernel source")
+                                if traffic is not None else
+                                (f"null: profiles/stage_kernel_{HEADLINE}_{n}.md is missing or was "
+                                 f"captured on another version of the stage kernel source"),
+                "peak_kind": f"{peak_kind} hbm_gbs",
                 "kernel": "stage_kernel (fused RHS + RK stage)", "stage_ms": round(stage_ms, 4),
                 "alg_bytes_per_launch": alg_bytes_launch}
+    # the arithmetic ceiling: the oracle-counted flops of one stage at this
+    # run's stage time against the FP32 peak of the unit counts and clock
+    flops_pp = op_tally_flops(cfg.split)
+    roof_alu = None
+    if flops_pp is not None:
+        sms = torch.cuda.get_device_properties(dev).multi_processor_count
+        peak_alu = fp32_peak_tflops(sms, peaks.get("sm_max_mhz", 2032.0))
+        ach_alu = flops_pp * n ** 3 / (stage_ms * 1e-3) / 1e12
+        roof_alu = {"bound": "alu", "achieved": round(ach_alu, 2), "peak": round(peak_alu, 2),
+                    "unit": "TFLOP/s", "frac": round(ach_alu / peak_alu, 4),
+                    "flops_per_point_stage": flops_pp,
+                    "flops_source": "profiles/op_tally.md: the oracle's formulas, each distinct "
+                                    "operation counted once (tests/op_tally.py)",
+                    "peak_kind": f"derived: {sms} SMs x 128 FP32 lanes x 2 flops (FMA) x "
+                                 f"{peaks.get('sm_max_mhz', 2032.0):.0f} MHz"}
     # the ceiling the FP16-storage stage actually meets: instruction issue (148 SMs x
     # 4 schedulers x one warp instruction of 32 threads per clock at 2032 MHz)
     ipp = profile_instr_per_point(HEADLINE, n)
@@ -511,11 +569,50 @@ def run_ours(args, rank, world, local):
     if dist is not None:
         dist.destroy_process_group()
     return {
-        "value": value, "ms_per_step": ms_step, "roofline": roofline,
-        "roofline_issue": issue_roof, "e2e": e2e,
+        "value": value, "ms_per_step": ms / K, "replicas": replicas, "slab": slab_run,
+        "roofline": roofline,
+        "roofline_issue": issue_roof, "roofline_alu": roof_alu, "e2e": e2e,
         "gpu_launches": launches, "clocks": clk.summary(), "modes": modes,
         "diag_last": dict(zip(tgv.DIAG_NAMES, diag_last)), "dt": dt, **extra,
     }
+
+
+def run_slab(tgv, torch, dist, rank, world, dev, n, dt, K, W, barrier, max_over_ranks):
+    """One n^3 box of the headline mode split into z-slabs, one per rank: every
+    RK stage exchanges two ghost planes per field with each neighbour (NCCL
+    point-to-point) and runs the slab stage kernel; diagnostics every 10
+    steps, all-reduced.  Time: K steps, max over ranks."""
+    from paper_2505_20911_b300 import slab
+    cfg = mode_config(tgv, n, HEADLINE)
+    z0, nz = slab.slab_bounds(n, world, rank)
+    dom = slab.SlabDomain(cfg, [(z0, nz)], rank, world, dist, dev)
+    dom.init()
+    diag = torch.empty(tgv.TGV_DIAG_COUNT, dtype=torch.float64, device=dev)
+
+    def steps(count):
+        for m in range(count):
+            if m % DIAG_EVERY == 0:
+                dom.step(dt, 1, diag=diag)
+                dist.all_reduce(diag)
+            else:
+                dom.step(dt, 1)
+
+    steps(W)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    barrier()
+    e0.record()
+    steps(K)
+    e1.record()
+    barrier()
+    ms = max_over_ranks(e0.elapsed_time(e1))
+    halo_bytes = 2 * 2 * 5 * n * n * torch.tensor([], dtype=cfg.q_dtype).element_size()
+    return {"value": n ** 3 * K / (ms * 1e-3), "ms": ms, "ms_per_step": ms / K,
+            "scaling": "strong", "planes_per_rank": nz,
+            "halo_bytes_per_stage_per_rank": halo_bytes,
+            "what": f"one {n}^3 box in z-slabs over {world} ranks, 2 ghost planes per field "
+                    f"exchanged with each neighbour before every RK stage (NCCL), diagnostics "
+                    f"all-reduced every {DIAG_EVERY} steps",
+            "K": dict(zip(tgv.DIAG_NAMES, diag.cpu().tolist()))["K"]}
 
 
 def extra_workloads(args, tgv, torch, dev, stream, peaks):
@@ -641,33 +738,58 @@ def extra_workloads(args, tgv, torch, dev, stream, peaks):
 
 
 # ------------------------------------------------------------ CPU oracle legs
-def oracle_sample(n_sample, steps=1):
+def oracle_sample(n_sample, steps=1, dt=None):
     """Time `steps` RK3 steps of the FP64 oracle on an n_sample^3 TGV."""
-    import torch
     import oracle
     flow = oracle.Flow(n=n_sample)
     q = oracle.initial_condition(flow)
+    dt = dt if dt is not None else DT_DEFAULT * 256.0 / n_sample
     t0 = time.perf_counter()
     for _ in range(steps):
-        q = oracle.rk3_step(flow, q, DT_DEFAULT * 256.0 / n_sample)
+        q = oracle.rk3_step(flow, q, dt)
     el = time.perf_counter() - t0
     return n_sample ** 3 * steps / el, el
 
 
+def cpu_model() -> str:
+    try:
+        for line in open("/proc/cpuinfo"):
+            if line.startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    return "unknown"
+
+
 def cpu_baseline(n):
-    """One RK substep (a third of a step) of the oracle on the full grid."""
+    """The oracle as it stands on the host cores: one RK substep (a third of a
+    step) on the full n^3 grid with all threads (the line's value), the
+    32^3 x 100-step run of the small configuration in full, with all threads
+    and on one thread."""
     import torch
     import oracle
+    threads = torch.get_num_threads()
     flow = oracle.Flow(n=n)
     q = oracle.initial_condition(flow)
     qt = torch.zeros_like(q)
     t0 = time.perf_counter()
     oracle.rk_substep(flow, q, qt, 0, DT_DEFAULT * 256.0 / n)
     el = time.perf_counter() - t0
-    return {"value": n ** 3 / (3.0 * el), "unit": UNIT, "cores": torch.get_num_threads(),
-            "kind": "oracle",
+    small, _ = oracle_sample(32, 100, dt=0.004)
+    torch.set_num_threads(1)
+    try:
+        single, el1 = oracle_sample(32, 100, dt=0.004)
+    finally:
+        torch.set_num_threads(threads)
+    return {"value": n ** 3 / (3.0 * el), "unit": UNIT, "cores": threads, "kind": "oracle",
+            "cpu_model": cpu_model(), "nproc": os.cpu_count(),
             "sample": f"1 RK substep (1/3 step) of the FP64 oracle on the full {n}^3 TGV grid, "
-                      f"{el:.1f} s on the host cores, scaled to point-steps/s"}
+                      f"{el:.1f} s on {threads} host threads, scaled to point-steps/s",
+            "tgv32_100_steps_all_core": {"value": small, "unit": UNIT, "threads": threads,
+                                         "sample": "32^3 TGV, dt 0.004, 100 RK3 steps in full"},
+            "tgv32_single_thread": {"value": single, "unit": UNIT, "threads": 1,
+                                    "seconds": el1,
+                                    "sample": "32^3 TGV, dt 0.004, 100 RK3 steps in full on one thread"}}
 
 
 def run_reference(args, rank, world):
@@ -710,7 +832,7 @@ def main():
         return
     rank, world, local = dist_env()
     base = {"metric": METRIC, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-            "warmup": max(args.warmup, 3), "higher_is_better": True, "scaling": "weak",
+            "warmup": max(args.warmup, 3), "higher_is_better": True, "scaling": "strong",
             "vs_baseline": None, "data": "synthetic (analytic Taylor-Green initial field)"}
     config = {"workload": f"TGV {args.n}^3 precision sweep (headline: HPSP, Q FP32 / Qt FP16 "
                           f"storage, FP32 compute)",
@@ -718,7 +840,7 @@ def main():
               "dt": DT_DEFAULT * 256.0 / args.n, "diag_every": DIAG_EVERY,
               "split": "blaisdell", "l2": "inputs larger than L2: Q in, Q out and Qt of the "
                                           "headline mode are each above 126 MB at 256^3",
-              "parallelism": f"replicas x{world}"}
+              "parallelism": "one GPU" if world == 1 else f"z-slabs x{world} (one box)"}
     if args.impl == "reference":
         ref = run_reference(args, rank, world)
         if rank == 0:
@@ -735,10 +857,11 @@ def main():
         return
     line = dict(base, value=res["value"], ms_per_step=res["ms_per_step"], dtype="f32",
                 config=config, roofline=res["roofline"], roofline_issue=res["roofline_issue"],
+                roofline_alu=res["roofline_alu"],
                 e2e=res["e2e"], gpu_launches=res["gpu_launches"], clocks=res["clocks"], modes=res["modes"],
                 diag_last=res["diag_last"])
-    for key in ("n512", "tgsym_256", "graph_32", "adjoint_64", "ensemble_48"):
-        if key in res:
+    for key in ("replicas", "slab", "n512", "tgsym_256", "graph_32", "adjoint_64", "ensemble_48"):
+        if res.get(key) is not None:
             line[key] = res[key]
     if world == 1 and not args.no_cpu:
         line["cpu_baseline"] = cpu_baseline(args.n)

@@ -341,6 +341,69 @@ int32_t tgv_run_host_stream(const tgv_config* cfg, int32_t count, const void* co
                             int32_t diag_every, double* diag_host, void* dev_workspace,
                             size_t ws_bytes, void* compute_stream, void* copy_stream);
 
+/*
+ * Z-slab domain decomposition (the parallel strategy of Sec. 4.3: every
+ * process owns a block of the grid and exchanges halo points with its
+ * neighbours before each residual evaluation; here a block is a slab of
+ * whole z planes of the periodic box, one per GPU, and the halos are
+ * exchanged in the storage type of Q).
+ *
+ * tgv_slab: owned planes z0 .. z0+nz-1 of the periodic N^3 box (nz >= 2).
+ * Slab state layout: 5 fields, each (nz + 4) planes of N x N points, x
+ * fastest: planes 0-1 are ghosts (copies of global planes z0-2, z0-1, wrapped),
+ * planes 2 .. nz+1 the owned planes, planes nz+2, nz+3 ghosts (global z0+nz,
+ * z0+nz+1, wrapped): element (c, k, j, i) at ((c*(nz+4) + k)*N + j)*N + i.
+ * Two ghost planes match the z reach of every term of the residual.
+ * A slab's Qt holds only the owned planes: ((c*nz + k)*N + j)*N + i.
+ * TGV_FLAG_SYMMETRIC is not supported (TGV_ERR_UNSUPPORTED).
+ */
+typedef struct tgv_slab {
+  int32_t z0; /* first owned global plane */
+  int32_t nz; /* owned planes, >= 2      */
+} tgv_slab;
+
+/* Bytes of a slab state (5 (nz+4) N^2 elements of q_storage) and of its Qt
+ * (5 nz N^2 of qt_storage); 0 if cfg or slab is invalid. */
+size_t tgv_slab_state_bytes(const tgv_config* cfg, const tgv_slab* slab);
+size_t tgv_slab_qt_bytes(const tgv_config* cfg, const tgv_slab* slab);
+
+/* Taylor-Green initial condition (Sec. 4.1, Eqs. 6-10) on the owned planes
+ * of a slab state q (device); the ghost planes are not written. */
+int32_t tgv_slab_init(const tgv_config* cfg, const tgv_slab* slab, void* q, void* stream);
+
+/*
+ * One RK substep i in {0,1,2} (Sec. 3.1, Eqs. 3-4) of a slab: the fused stage
+ * kernel of rk_step on the owned planes of q_in (device, slab layout; its
+ * ghost planes must hold the neighbours' current planes), written to the
+ * owned planes of q_out (device, slab layout, != q_in; ghosts untouched).
+ * qt (device, slab Qt layout) is internal scratch as in rk_step (the
+ * increment kept divided by dt; ignored on entry for i = 0, not written for
+ * i = 2), so three substeps with an exchange before each equal one rk_step
+ * step of the whole box, bit for bit, on every owned plane.
+ * diag_dev (nullable; device double[TGV_DIAG_COUNT]): the diagnostics of
+ * q_in's owned planes as contributions to the whole box's means (sums over
+ * the slab divided by N^3; eps^S by N^3 Re): summed over all slabs they are
+ * diagnostics_reduce of the box.  workspace: tgv_workspace_bytes(cfg) bytes
+ * when diag_dev is given.  Returns TGV_ERR_UNSTABLE_DT like rk_step.
+ */
+int32_t tgv_slab_substep(const tgv_config* cfg, const tgv_slab* slab, const void* q_in,
+                         void* q_out, void* qt, int32_t i, double dt, double* diag_dev,
+                         void* workspace, size_t ws_bytes, void* stream);
+
+/*
+ * Ghost exchange among `count` slabs of one box that all live on the current
+ * device: slabs[r] must tile [0, N) in order (slabs[0].z0 = 0, each slab
+ * starting where the previous ends); q[r] is slab r's state (device, slab
+ * layout).  Fills every slab's four ghost planes from its periodic
+ * neighbours with 20 device-to-device copies per slab (per field, the two
+ * top owned planes of the slab below and the two bottom owned planes of the
+ * slab above); one slab (count = 1) wraps onto itself.  Between processes
+ * on different GPUs the same blocks are exchanged with point-to-point
+ * messages instead (the Python binding, over NCCL).
+ */
+int32_t tgv_slab_exchange_local(const tgv_config* cfg, int32_t count, const tgv_slab* slabs,
+                                void* const* q, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

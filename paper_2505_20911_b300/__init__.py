@@ -305,6 +305,60 @@ def tgv_run_host_stream(cfg: Config, qs_host_in, qs_host_out, dt: float, nsteps:
           "tgv_run_host_stream")
 
 
+# ------------------------------------------------------------------ z-slabs
+def _slab(z0: int, nz: int) -> _abi.tgv_slab:
+    return _abi.tgv_slab(z0=int(z0), nz=int(nz))
+
+
+def tgv_slab_state_bytes(cfg: Config, z0: int, nz: int) -> int:
+    return lib().tgv_slab_state_bytes(C.byref(cfg.c()), C.byref(_slab(z0, nz)))
+
+
+def tgv_slab_qt_bytes(cfg: Config, z0: int, nz: int) -> int:
+    return lib().tgv_slab_qt_bytes(C.byref(cfg.c()), C.byref(_slab(z0, nz)))
+
+
+def empty_slab_state(cfg: Config, nz: int, device="cuda") -> torch.Tensor:
+    """A (5, nz + 4, N, N) slab state of the Q storage type (2 ghost planes
+    below and above the owned planes)."""
+    return torch.empty((5, nz + 4, cfg.n, cfg.n), dtype=cfg.q_dtype, device=device)
+
+
+def empty_slab_qt(cfg: Config, nz: int, device="cuda") -> torch.Tensor:
+    return torch.empty((5, nz, cfg.n, cfg.n), dtype=cfg.qt_dtype, device=device)
+
+
+def tgv_slab_init(cfg: Config, z0: int, nz: int, q, stream=None) -> None:
+    pq = _dev(q, "q", cfg.q_dtype, tgv_slab_state_bytes(cfg, z0, nz))
+    check(lib().tgv_slab_init(C.byref(cfg.c()), C.byref(_slab(z0, nz)), pq, _stream(stream)),
+          "tgv_slab_init")
+
+
+def tgv_slab_substep(cfg: Config, z0: int, nz: int, q_in, q_out, qt, i: int, dt: float,
+                     diag=None, workspace=None, stream=None) -> None:
+    qb = tgv_slab_state_bytes(cfg, z0, nz)
+    pi, po = _dev(q_in, "q_in", cfg.q_dtype, qb), _dev(q_out, "q_out", cfg.q_dtype, qb)
+    pt = _dev(qt, "qt", cfg.qt_dtype, tgv_slab_qt_bytes(cfg, z0, nz))
+    pd = _dev(diag, "diag", torch.float64, TGV_DIAG_COUNT * 8) if diag is not None else None
+    pw, ws_bytes = _ws(workspace)
+    check(lib().tgv_slab_substep(C.byref(cfg.c()), C.byref(_slab(z0, nz)), pi, po, pt, int(i),
+                                 float(dt), pd, pw, ws_bytes, _stream(stream)),
+          "tgv_slab_substep")
+
+
+def tgv_slab_exchange_local(cfg: Config, slabs, qs, stream=None) -> None:
+    """Ghost exchange among slabs (list of (z0, nz), tiling [0, N) in order)
+    whose states qs all live on the current device."""
+    if len(slabs) != len(qs) or not slabs:
+        raise ValueError("one state per slab")
+    ptrs = [_dev(q, f"q[{r}]", cfg.q_dtype, tgv_slab_state_bytes(cfg, *sl))
+            for r, (sl, q) in enumerate(zip(slabs, qs))]
+    arr = (_abi.tgv_slab * len(slabs))(*[_slab(*sl) for sl in slabs])
+    check(lib().tgv_slab_exchange_local(C.byref(cfg.c()), len(slabs), arr,
+                                        (C.c_void_p * len(qs))(*ptrs), _stream(stream)),
+          "tgv_slab_exchange_local")
+
+
 def diagnostics(cfg: Config, q: torch.Tensor, workspace=None) -> dict:
     """Convenience: diagnostics_reduce into a fresh tensor, returned as a dict."""
     ws = workspace if workspace is not None else empty_workspace(cfg, q.device)

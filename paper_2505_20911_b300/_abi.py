@@ -37,6 +37,10 @@ class tgv_config(C.Structure):
     ]
 
 
+class tgv_slab(C.Structure):
+    _fields_ = [("z0", C.c_int32), ("nz", C.c_int32)]
+
+
 class TGVError(RuntimeError):
     def __init__(self, status: int, where: str):
         self.status = status
@@ -47,6 +51,7 @@ _lib = None
 
 _P = C.c_void_p
 _CFG = C.POINTER(tgv_config)
+_SLAB = C.POINTER(tgv_slab)
 # name -> (restype, argtypes)
 SIGNATURES = {
     "tgv_abi_version": (C.c_int32, []),
@@ -78,6 +83,12 @@ SIGNATURES = {
     "tgv_ensemble_run": (C.c_int32, [_P, C.c_int32, _P]),
     "tgv_ensemble_info": (C.c_int32, [_P] + [C.POINTER(C.c_int32)] * 5),
     "tgv_ensemble_destroy": (C.c_int32, [_P]),
+    "tgv_slab_state_bytes": (C.c_size_t, [_CFG, _SLAB]),
+    "tgv_slab_qt_bytes": (C.c_size_t, [_CFG, _SLAB]),
+    "tgv_slab_init": (C.c_int32, [_CFG, _SLAB, _P, _P]),
+    "tgv_slab_substep": (C.c_int32, [_CFG, _SLAB, _P, _P, _P, C.c_int32, C.c_double, _P, _P,
+                                     C.c_size_t, _P]),
+    "tgv_slab_exchange_local": (C.c_int32, [_CFG, C.c_int32, _SLAB, C.POINTER(C.c_void_p), _P]),
     "tgv_run_host_workspace_bytes": (C.c_size_t, [_CFG, C.c_int32, C.c_int32]),
     "tgv_run_host": (C.c_int32, [_CFG, _P, _P, C.c_double, C.c_int32, C.c_int32, _P, _P,
                                  C.c_size_t, _P]),

@@ -118,9 +118,10 @@ static int pick_tile(const tgv_config& c) {
 // with it the diagnostics partials of a fused launch).
 constexpr int MAX_ZCHUNKS = 16;
 
-static long long stage_ctas(const tgv_config& c, int tile, int zc) {
+// CTAs of one stage launch over nzl planes (N for the periodic box).
+static long long stage_ctas(const tgv_config& c, int tile, int zc, int nzl) {
   const int tx = tile_tx(c.compute, tile), ty = tile_ty(c.compute, tile);
-  return (long long)((c.n + tx - 1) / tx) * ((c.n + ty - 1) / ty) * ((c.n + zc - 1) / zc);
+  return (long long)((c.n + tx - 1) / tx) * ((c.n + ty - 1) / ty) * ((nzl + zc - 1) / zc);
 }
 
 // Per-device caches (SM count; resident CTAs per SM of each stage kernel).
@@ -151,18 +152,19 @@ static int stage_occ(int dev, int mode, int tile) {
 }
 
 // z planes per CTA: balance whole waves of resident CTAs against the 4 extra
-// halo planes each chunk reads.
-static int pick_zchunk(const tgv_config& c, int tile, int occupancy, int sms) {
-  if (c.zchunk > 0) return c.zchunk;
+// halo planes each chunk reads; nzl planes are advanced (N for the periodic
+// box, the owned planes of a slab).
+static int pick_zchunk(const tgv_config& c, int tile, int occupancy, int sms, int nzl) {
+  if (c.zchunk > 0) return c.zchunk < nzl ? c.zchunk : nzl;
   const int n = c.n;
   const int tx = tile_tx(c.compute, tile), ty = tile_ty(c.compute, tile);
   const long long tiles = (long long)((n + tx - 1) / tx) * ((n + ty - 1) / ty);
   const long long conc = (long long)(occupancy > 0 ? occupancy : 1) * (sms > 0 ? sms : 148);
   double best = -1.0;
-  int best_zc = n;
-  for (int chunks = 1; chunks <= n / 8 && chunks <= MAX_ZCHUNKS; ++chunks) {
-    const int zc = (n + chunks - 1) / chunks;
-    const long long ctas = tiles * ((n + zc - 1) / zc);
+  int best_zc = nzl;
+  for (int chunks = 1; chunks <= nzl / 8 && chunks <= MAX_ZCHUNKS; ++chunks) {
+    const int zc = (nzl + chunks - 1) / chunks;
+    const long long ctas = tiles * ((nzl + zc - 1) / zc);
     const long long waves = (ctas + conc - 1) / conc;
     const double fill = (double)ctas / (double)(waves * conc);
     const double eff = fill * (double)zc / (double)(zc + 4);
@@ -229,7 +231,7 @@ size_t tgv_workspace_bytes(const tgv_config* cfg) {
   long long blocks = DIAG_MAX_BLOCKS;
   for (int t = 0; t < NUM_TILES; ++t) {
     const int zc = cfg->zchunk > 0 ? cfg->zchunk : (cfg->n + MAX_ZCHUNKS - 1) / MAX_ZCHUNKS;
-    const long long b = stage_ctas(*cfg, t, zc);
+    const long long b = stage_ctas(*cfg, t, zc, cfg->n);
     if (b > blocks) blocks = b;
   }
   return (size_t)blocks * TGV_DIAG_COUNT * sizeof(double);
@@ -240,7 +242,9 @@ int32_t tgv_init(const tgv_config* cfg, void* q, void* stream) {
   if (s != TGV_OK) return s;
   if (!q) return TGV_ERR_ARG;
   const Problem P = make_problem(*cfg);
-  TGV_CUDA_TRY(mode_launchers(find_mode(*cfg)).init(P, q, (cudaStream_t)stream));
+  const long long n3 = (long long)cfg->n * cfg->n * cfg->n;
+  const ZLayout L{0, cfg->n, 0, n3};
+  TGV_CUDA_TRY(mode_launchers(find_mode(*cfg)).init(P, q, L, (cudaStream_t)stream));
   return TGV_OK;
 }
 
@@ -256,11 +260,12 @@ static int32_t launch_stage_common(const tgv_config* cfg, const StageArgs& S, bo
   if (dev < 0) return TGV_ERR_CUDA;
   const int occ = stage_occ(dev, m, tile);
   if (occ <= 0) return TGV_ERR_CUDA;
-  const int zc = pick_zchunk(*cfg, tile, occ, device_sms(dev));
+  const int nzl = S.nzl > 0 ? S.nzl : cfg->n;
+  const int zc = pick_zchunk(*cfg, tile, occ, device_sms(dev), nzl);
   StageArgs A = S;
   A.zchunk = zc;
   const Problem P = make_problem(*cfg);
-  if (ctas) *ctas = stage_ctas(*cfg, tile, zc);
+  if (ctas) *ctas = stage_ctas(*cfg, tile, zc, nzl);
   const int v = cfg->split_form == TGV_SPLIT_KGP      ? SPL_KGP
                 : cfg->split_form == TGV_SPLIT_KEEP     ? SPL_KEEP
                 : cfg->split_form == TGV_SPLIT_FEIEREISEN ? SPL_FEIER
@@ -507,6 +512,114 @@ int32_t tgv_run_host_stream(const tgv_config* cfg, int32_t count, const void* co
   }
   if ((s = copy_out(count - 1)) != TGV_OK) return cleanup(s);
   return cleanup(TGV_OK);
+}
+
+// ------------------------------------------------------------ z-slabs
+static int32_t check_slab(const tgv_config* cfg, const tgv_slab* sl) {
+  int32_t s = check(cfg);
+  if (s != TGV_OK) return s;
+  if (!sl || sl->nz < 2 || sl->z0 < 0 || sl->z0 + sl->nz > cfg->n) return TGV_ERR_ARG;
+  if (cfg->flags & TGV_FLAG_SYMMETRIC) return TGV_ERR_UNSUPPORTED;
+  return TGV_OK;
+}
+
+static long long slab_fs(const tgv_config* cfg, const tgv_slab* sl) {
+  return (long long)(sl->nz + 4) * cfg->n * cfg->n;
+}
+
+size_t tgv_slab_state_bytes(const tgv_config* cfg, const tgv_slab* slab) {
+  if (check_slab(cfg, slab) != TGV_OK) return 0;
+  return 5 * (size_t)slab_fs(cfg, slab) * dtype_size(cfg->q_storage);
+}
+
+size_t tgv_slab_qt_bytes(const tgv_config* cfg, const tgv_slab* slab) {
+  if (check_slab(cfg, slab) != TGV_OK) return 0;
+  return 5 * (size_t)slab->nz * cfg->n * cfg->n * dtype_size(cfg->qt_storage);
+}
+
+int32_t tgv_slab_init(const tgv_config* cfg, const tgv_slab* slab, void* q, void* stream) {
+  int32_t s = check_slab(cfg, slab);
+  if (s != TGV_OK) return s;
+  if (!q) return TGV_ERR_ARG;
+  const Problem P = make_problem(*cfg);
+  const ZLayout L{slab->z0, slab->nz, 2, slab_fs(cfg, slab)};
+  TGV_CUDA_TRY(mode_launchers(find_mode(*cfg)).init(P, q, L, (cudaStream_t)stream));
+  return TGV_OK;
+}
+
+int32_t tgv_slab_substep(const tgv_config* cfg, const tgv_slab* slab, const void* q_in,
+                         void* q_out, void* qt, int32_t i, double dt, double* diag_dev,
+                         void* workspace, size_t ws_bytes, void* stream) {
+  int32_t s = check_slab(cfg, slab);
+  if (s != TGV_OK) return s;
+  if (!q_in || !q_out || !qt || q_in == q_out || i < 0 || i > 2 || !std::isfinite(dt) ||
+      !(dt > 0.0))
+    return TGV_ERR_ARG;
+  if (diag_dev && (!workspace || ws_bytes < tgv_workspace_bytes(cfg))) return TGV_ERR_WORKSPACE;
+  if (!(cfg->flags & TGV_FLAG_ALLOW_UNSTABLE_DT) && dt > tgv_dt_max(cfg)) return TGV_ERR_UNSTABLE_DT;
+  StageArgs S;
+  std::memset(&S, 0, sizeof(S));
+  S.q_in = q_in;
+  S.q_out = q_out;
+  S.qt = qt;
+  S.diag_part = diag_dev ? static_cast<double*>(workspace) : nullptr;
+  S.a = RK_A[i];
+  S.b = RK_B[i];
+  S.dt = dt;
+  S.read_qt = (i != 0);
+  S.write_qt = (i != 2);   // as rk_step: the last substep's increment is never read
+  S.scaled_qt = 1;         // as rk_step: the increment is kept divided by dt
+  S.bdt = RK_B[i] * dt;
+  S.zg = 2;
+  S.nzl = slab->nz;
+  S.fs_q = slab_fs(cfg, slab);
+  S.fs_t = (long long)slab->nz * cfg->n * cfg->n;
+  long long ctas = 0;
+  s = launch_stage_common(cfg, S, false, (cudaStream_t)stream, &ctas);
+  if (s != TGV_OK) return s;
+  if (diag_dev) {
+    const Problem P = make_problem(*cfg);
+    diag_final_kernel<<<1, 32 * TGV_DIAG_COUNT, 0, (cudaStream_t)stream>>>(P, S.diag_part,
+                                                                         (int)ctas, diag_dev);
+    TGV_CUDA_TRY(cudaGetLastError());
+  }
+  return TGV_OK;
+}
+
+int32_t tgv_slab_exchange_local(const tgv_config* cfg, int32_t count, const tgv_slab* slabs,
+                                void* const* q, void* stream) {
+  int32_t s = check(cfg);
+  if (s != TGV_OK) return s;
+  if (count < 1 || !slabs || !q) return TGV_ERR_ARG;
+  int32_t z = 0;
+  for (int32_t r = 0; r < count; ++r) {  // the slabs tile [0, N) in order
+    if ((s = check_slab(cfg, &slabs[r])) != TGV_OK) return s;
+    if (slabs[r].z0 != z || !q[r]) return TGV_ERR_ARG;
+    z += slabs[r].nz;
+  }
+  if (z != cfg->n) return TGV_ERR_ARG;
+  const size_t es = dtype_size(cfg->q_storage);
+  const size_t nn = (size_t)cfg->n * cfg->n, blk = 2 * nn * es;
+  cudaStream_t st = (cudaStream_t)stream;
+  for (int32_t r = 0; r < count; ++r) {
+    const int32_t lo = (r + count - 1) % count, hi = (r + 1) % count;
+    char* dst = static_cast<char*>(q[r]);
+    const char* below = static_cast<const char*>(q[lo]);
+    const char* above = static_cast<const char*>(q[hi]);
+    const size_t fs = (size_t)slab_fs(cfg, &slabs[r]) * es;
+    const size_t fs_lo = (size_t)slab_fs(cfg, &slabs[lo]) * es;
+    const size_t fs_hi = (size_t)slab_fs(cfg, &slabs[hi]) * es;
+    for (int c = 0; c < 5; ++c) {
+      // ghosts 0-1 <- the two top owned planes of the slab below (its planes nz, nz+1)
+      TGV_CUDA_TRY(cudaMemcpyAsync(dst + c * fs, below + c * fs_lo + (size_t)slabs[lo].nz * nn * es,
+                                   blk, cudaMemcpyDeviceToDevice, st));
+      // ghosts nz+2, nz+3 <- the two bottom owned planes of the slab above (its planes 2, 3)
+      TGV_CUDA_TRY(cudaMemcpyAsync(dst + c * fs + (size_t)(slabs[r].nz + 2) * nn * es,
+                                   above + c * fs_hi + 2 * nn * es, blk,
+                                   cudaMemcpyDeviceToDevice, st));
+    }
+  }
+  return TGV_OK;
 }
 
 }  // extern "C"

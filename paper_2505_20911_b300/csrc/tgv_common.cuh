@@ -139,6 +139,21 @@ __host__ __device__ __forceinline__ int wrap_index(int i, int n, bool symmetric,
   return i < 0 ? 0 : (i >= n ? n - 1 : i);
 }
 
+// wrap_index for an index within one box length of the grid (i in [-n, 2n)),
+// without a division: the z planes a stage kernel visits (z0 - 2 .. z1 + 1).
+__host__ __device__ __forceinline__ int wrap_near(int i, int n, bool symmetric, bool* flipped) {
+  *flipped = false;
+  if (i < 0) {
+    if (symmetric) { *flipped = true; return -1 - i; }
+    return i + n;
+  }
+  if (i >= n) {
+    if (symmetric) { *flipped = true; return 2 * n - 1 - i; }
+    return i - n;
+  }
+  return i;
+}
+
 Problem make_problem(const tgv_config& c);
 
 // Storage-type tag -> C++ type.

@@ -64,6 +64,9 @@ ensemble_stage_kernel(const EnsTable T, const double a, const double b, const in
     S.scaled_qt = 1;  // as rk_step: Qt is internal scratch kept divided by dt
     S.bdt = b * I.dt;
     S.zchunk = I.zchunk;
+    S.zg = 0;  // the periodic box
+    S.nzl = 0;
+    S.fs_q = S.fs_t = 0;
     stage_tile<float, float, float, float, TX, TY, 2, EPI_RK, false>(I.P, S, bx * TX, by * TY,
                                                                       bz * I.zchunk, 0);
     __syncthreads();  // the next item reuses the shared-memory ring

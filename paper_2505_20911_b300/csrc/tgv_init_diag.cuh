@@ -5,14 +5,25 @@
 
 namespace tgv {
 
+// Where a state's planes live: owned planes are global z = z0 .. z0+nzl-1,
+// stored after zg ghost planes, fields fs elements apart.  The periodic box is
+// {0, N, 0, N^3}; a z-slab has zg = 2 and fs = (nzl + 4) N^2.
+struct ZLayout {
+  int z0, nzl, zg;
+  long long fs;
+};
+
 // Taylor-Green initial field (Sec. 4.1, Eqs. 6-10), evaluated in FP64 and
-// rounded once to the storage type (offset-encoded if requested).
+// rounded once to the storage type (offset-encoded if requested), on the
+// owned planes of layout L (ghost planes are not written).
 template <class TS>
-__global__ void init_kernel(const Problem P, TS* __restrict__ q) {
-  const long long n = P.n, nn = n * n, n3 = nn * n;
-  for (long long o = blockIdx.x * (long long)blockDim.x + threadIdx.x; o < n3;
+__global__ void init_kernel(const Problem P, TS* __restrict__ q, const ZLayout L) {
+  const long long n = P.n, nn = n * n, cnt = nn * L.nzl, fs = L.fs;
+  for (long long o = blockIdx.x * (long long)blockDim.x + threadIdx.x; o < cnt;
        o += (long long)gridDim.x * blockDim.x) {
-    const int i = (int)(o % n), j = (int)((o / n) % n), k = (int)(o / nn);
+    const int i = (int)(o % n), j = (int)((o / n) % n), kl = (int)(o / nn);
+    const int k = L.z0 + kl;
+    const long long d = o + (long long)L.zg * nn;
     const double x = (i + P.offset) * P.h, y = (j + P.offset) * P.h, z = (k + P.offset) * P.h;
     double sx, cx, sy, cy, sz, cz;
     sincos(x, &sx, &cx);
@@ -23,11 +34,11 @@ __global__ void init_kernel(const Problem P, TS* __restrict__ q) {
     const double p = 1.0 / P.gM2 + (c2x + c2y) * (2.0 + c2z) / 16.0;
     const double rho = P.gM2 * p;
     const double rhoE = p / P.gm1 + 0.5 * rho * (u * u + v * v);
-    q[o] = Num<TS>::from_f64(rho - P.rho0);
-    q[o + n3] = Num<TS>::from_f64(rho * u);
-    q[o + 2 * n3] = Num<TS>::from_f64(rho * v);
-    q[o + 3 * n3] = Num<TS>::from_f64(0.0);
-    q[o + 4 * n3] = Num<TS>::from_f64(rhoE - P.rhoE0);
+    q[d] = Num<TS>::from_f64(rho - P.rho0);
+    q[d + fs] = Num<TS>::from_f64(rho * u);
+    q[d + 2 * fs] = Num<TS>::from_f64(rho * v);
+    q[d + 3 * fs] = Num<TS>::from_f64(0.0);
+    q[d + 4 * fs] = Num<TS>::from_f64(rhoE - P.rhoE0);
   }
 }
 

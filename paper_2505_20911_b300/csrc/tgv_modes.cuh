@@ -43,7 +43,7 @@ inline int tile_ty(int comp, int t) { return comp == TGV_F64 ? TILE_TY_F64[t] : 
 
 using StageFn = cudaError_t (*)(const Problem&, const StageArgs&, int zchunk, cudaStream_t);
 using OccFn = int (*)();
-using InitFn = cudaError_t (*)(const Problem&, void*, cudaStream_t);
+using InitFn = cudaError_t (*)(const Problem&, void*, const ZLayout&, cudaStream_t);
 using DiagFn = cudaError_t (*)(const Problem&, const void*, double*, int, cudaStream_t);
 
 // Kernel variants by convective split family (SPL_QUAD, SPL_KGP, SPL_KEEP,
@@ -71,7 +71,8 @@ cudaError_t launch_stage(const Problem& P, const StageArgs& S, int zchunk, cudaS
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   const int n = P.n;
-  dim3 grid((n + TX - 1) / TX, (n + TY - 1) / TY, (n + zchunk - 1) / zchunk);
+  const int nzl = S.nzl > 0 ? S.nzl : n;
+  dim3 grid((n + TX - 1) / TX, (n + TY - 1) / TY, (nzl + zchunk - 1) / zchunk);
   dim3 block(TX / NP, TY);
   kern<<<grid, block, smem, st>>>(P, S);
   return cudaGetLastError();
@@ -91,12 +92,12 @@ int stage_occupancy() {
 }
 
 template <class TS>
-cudaError_t launch_init(const Problem& P, void* q, cudaStream_t st) {
-  const long long n3 = (long long)P.n * P.n * P.n;
+cudaError_t launch_init(const Problem& P, void* q, const ZLayout& L, cudaStream_t st) {
+  const long long cnt = (long long)P.n * P.n * L.nzl;
   const int threads = 256;
-  const long long blocks = (n3 + threads - 1) / threads;
+  const long long blocks = (cnt + threads - 1) / threads;
   init_kernel<TS><<<(unsigned)(blocks < 148 * 64 ? blocks : 148 * 64), threads, 0, st>>>(
-      P, static_cast<TS*>(q));
+      P, static_cast<TS*>(q), L);
   return cudaGetLastError();
 }
 

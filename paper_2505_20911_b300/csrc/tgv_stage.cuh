@@ -71,6 +71,13 @@ struct StageArgs {
                       //    multiply; rk_step's Qt is internal scratch
   double bdt;         // B_i * dt (scaled_qt)
   int zchunk;         // z planes per CTA
+  // z extent (0 = the periodic box: N planes, z wraps, field stride N^3).
+  // A z-slab: nzl owned planes, stored after zg ghost planes and followed by
+  // zg more in q_in / q_out (no wrap in z), field stride fs_q there; Qt and
+  // r_out hold the owned planes only, field stride fs_t.
+  int zg;
+  int nzl;
+  long long fs_q, fs_t;
 };
 
 // Ring-plane fields (compute type).  rho w is not kept: its taps are formed
@@ -102,13 +109,25 @@ struct Geo {
   static constexpr int PERH = (HU + NT - 1) / NT;
 };
 
-// Shared memory: ring, s_z ring, strips (compute type), then the cp.async
-// staging of one raw plane (storage type) and two raw Qt planes of the tile.
+// Raw-plane staging depth: with FP32 arithmetic on 16-bit storage, four
+// staged raw planes are kept (7 KB each for a 32x16 tile), so the RK epilogue
+// of centre plane k reads its own unit's Q_in from the staging of plane k
+// (staged three planes earlier and not yet overwritten); otherwise one.  (Four
+// FP32 planes would take the CTA to 220 KB of shared memory and leave the L1
+// cache too small for the cp.async traffic: measured 15% slower.)
+template <class TS, class TC>
+__host__ __device__ constexpr int raw_slots() {
+  return std::is_same<TC, float>::value && sizeof(TS) == 2 ? 4 : 1;
+}
+
+// Shared memory: ring, strips (compute type), then the cp.async staging of
+// the raw planes (storage type) and two raw Qt planes of the tile.
 template <class TS, class TT, class TC, int TX, int TY, int NP>
 constexpr size_t stage_smem_bytes() {
   using G = Geo<TX, TY, NP>;
   return sizeof(TC) * ((size_t)NSLOT * NFLD * G::PL + (size_t)NSTRIP * G::PL) +
-         sizeof(TS) * NP * 5 * (size_t)G::PLU + sizeof(TT) * NP * 2 * 5 * (size_t)G::NT;
+         sizeof(TS) * NP * 5 * (size_t)G::PLU * raw_slots<TS, TC>() +
+         sizeof(TT) * NP * 2 * 5 * (size_t)G::NT;
 }
 // Largest dynamic shared memory a stage CTA may request (B300: 227 KB per CTA,
 // less the static reduction buffer of the fused-diagnostics variant).
@@ -229,7 +248,9 @@ __device__ __forceinline__ void stage_tile(const Problem& P, const StageArgs& S,
   const int n = P.n;
   const long long nn = (long long)n * n, n3 = nn * n;
   const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * TXU + tx;
-  const int z1 = min(z0 + S.zchunk, n);
+  const int zg = S.zg, nzl = S.nzl > 0 ? S.nzl : n;
+  const long long fsq = S.fs_q > 0 ? S.fs_q : n3, fst = S.fs_t > 0 ? S.fs_t : n3;
+  const int z1 = min(z0 + S.zchunk, nzl);
   const TS* __restrict__ q_in = static_cast<const TS*>(S.q_in);
 
   const V c_inv12h = V::splat(cvt<TC>(P.inv12h)), c_inv12h2 = V::splat(cvt<TC>(P.inv12h2));
@@ -257,8 +278,12 @@ __device__ __forceinline__ void stage_tile(const Problem& P, const StageArgs& S,
   // left/right columns of rows 2..TY+1, rows TY+2..TY+3).
   using RawS = typename UnitIO<TC, NP, TS>::Raw;
   using RawT = typename UnitIO<TA, NP, TT>::Raw;
-  RawS* stage_q = reinterpret_cast<RawS*>(strips + NSTRIP * PL);       // [5][PLU]
-  RawT* stage_t = reinterpret_cast<RawT*>(stage_q + 5 * PLU);         // [2][5][NT]
+  constexpr int RS = raw_slots<TS, TC>();
+  RawS* stage_q = reinterpret_cast<RawS*>(strips + NSTRIP * PL);       // [RS][5][PLU]
+  RawT* stage_t = reinterpret_cast<RawT*>(stage_q + RS * 5 * PLU);    // [2][5][NT]
+  const int zbase = z0 - 2;
+  // staging slot of raw plane zl (RS is a power of two)
+  auto raw_plane = [&](int zl) -> RawS* { return stage_q + ((zl - zbase) & (RS - 1)) * 5 * PLU; };
   int goff[PERU], eoff[PERU], tform[PERU];  // tform: 1 swap lanes, 2 -rho u, 4 -rho v
   const bool sym = P.symmetric != 0;
 #pragma unroll
@@ -300,17 +325,18 @@ __device__ __forceinline__ void stage_tile(const Problem& P, const StageArgs& S,
   }
   const long long tile_off = (long long)(y0 + ty) * n + (x0 + NP * tx);
   const bool active_xy = (x0 + NP * tx < n) && (y0 + ty < n);
-  auto prefetch = [&](int zl) {  // cp.async of raw plane zl into the staging
+  auto prefetch = [&](int zl) {  // cp.async of raw plane zl into its staging slot
     bool fz;
-    const int zw = wrap_index(zl, n, sym, &fz);
+    const int zw = zg ? zl + zg : wrap_near(zl, n, sym, &fz);
     const long long zoff = (long long)zw * nn;
+    RawS* dst = raw_plane(zl);
 #pragma unroll
     for (int r = 0; r < PERU; ++r) {
       if (goff[r] >= 0) {
         const int q = tid + r * NT;
 #pragma unroll
         for (int c = 0; c < 5; ++c)
-          cp_async<sizeof(RawS)>(stage_q + c * PLU + q, q_in + zoff + goff[r] + c * n3);
+          cp_async<sizeof(RawS)>(dst + c * PLU + q, q_in + zoff + goff[r] + c * fsq);
       }
     }
   };
@@ -320,40 +346,40 @@ __device__ __forceinline__ void stage_tile(const Problem& P, const StageArgs& S,
     RawT* dst = stage_t + (kq & 1) * 5 * NT;
 #pragma unroll
     for (int c = 0; c < 5; ++c)
-      cp_async<sizeof(RawT)>(dst + c * NT + tid, qt + (long long)kq * nn + tile_off + c * n3);
+      cp_async<sizeof(RawT)>(dst + c * NT + tid, qt + (long long)kq * nn + tile_off + c * fst);
   };
-  // The epilogue's Q_in of the own unit, in storage precision: with FP32
-  // compute and storage of at most 32 bits it is carried from the plane
-  // loader in a three-plane register queue (planes zl, zl-1, zl-2; zeroed
-  // first, so no entry is read before it is written), otherwise re-read at the
-  // start of phase B (a cache hit: the loader read it two planes earlier).
-  // Measured at 256^3: the queue is 3-4% faster in the FP32-compute modes,
-  // the re-read 15% faster in pure half.
-  constexpr bool QIN_QUEUE = std::is_same<TC, float>::value && sizeof(TS) <= 4;
-  RawS qin_q[QIN_QUEUE ? 3 : 1][5];
+  // The epilogue's Q_in of the own unit, in storage precision:
+  //  - four raw planes staged (raw_slots): read from the staging of its plane;
+  //  - FP32 storage and arithmetic, plain encoding: rho, rho u, rho v and
+  //    rho E of the centre plane are already in registers as exact copies of
+  //    the stored values (fc below); rho w, which the ring does not hold, is
+  //    carried from the plane loader in a three-plane register queue (planes
+  //    zl, zl-1, zl-2; zeroed first, so no entry is read before it is written);
+  //  - otherwise: re-read from global memory at the start of phase B (a cache
+  //    hit: the loader read it two planes earlier).
+  constexpr bool QIN_FC = std::is_same<TS, float>::value && std::is_same<TC, float>::value;
+  const bool qin_fc = QIN_FC && P.encoding == TGV_ENC_PLAIN;
+  RawS qin_raw[5];
+  RawS qw_q[QIN_FC ? 3 : 1];
 #pragma unroll
-  for (int d = 0; d < (QIN_QUEUE ? 3 : 1); ++d)
-#pragma unroll
-    for (int c = 0; c < 5; ++c) qin_q[d][c] = RawS{};
+  for (int d = 0; d < (QIN_FC ? 3 : 1); ++d) qw_q[d] = RawS{};
   auto commit = [&](int slot, int zl) {  // staged raw plane -> primitives in the ring
     TC* base = ring + slot * NFLD * PL;
     bool fz;
-    wrap_index(zl, n, sym, &fz);
+    wrap_near(zl, n, sym, &fz);
+    const RawS* src = raw_plane(zl);
 #pragma unroll
     for (int r = 0; r < PERU; ++r) {
       const int q = tid + r * NT;
       if (q < PLU) {
         RawS raw[5];
 #pragma unroll
-        for (int c = 0; c < 5; ++c) raw[c] = stage_q[c * PLU + q];
-        if constexpr (QIN_QUEUE) {
+        for (int c = 0; c < 5; ++c) raw[c] = src[c * PLU + q];
+        if constexpr (QIN_FC) {
           if (r == 0) {
-#pragma unroll
-            for (int c = 0; c < 5; ++c) {
-              qin_q[2][c] = qin_q[1][c];
-              qin_q[1][c] = qin_q[0][c];
-              qin_q[0][c] = raw[c];
-            }
+            qw_q[2] = qw_q[1];
+            qw_q[1] = qw_q[0];
+            qw_q[0] = raw[3];
           }
         }
         const int e = eoff[r];
@@ -412,7 +438,6 @@ __device__ __forceinline__ void stage_tile(const Problem& P, const StageArgs& S,
     for (int m = 0; m < TGV_DIAG_COUNT; ++m) dacc[m] = 0.0;
   }
 
-  const int zbase = z0 - 2;
   const int rxc = 2 + NP * tx, ryc = 2 + ty;
   const int ec = ryc * RX + rxc;        // unit centre in plane layout
   const V zero = V::splat(cvt<TC>(0.0));
@@ -420,10 +445,34 @@ __device__ __forceinline__ void stage_tile(const Problem& P, const StageArgs& S,
 #pragma unroll
   for (int d = 0; d < 5; ++d) szq[d] = zero;
 
+  // halo-strip unit of this thread (fixed for the whole z march): its offset
+  // in the plane layout and kind (1: x-halo unit, s_x and G_x; 2: y-halo
+  // unit, s_y and G_y; 0: none)
+  int strip_e[G::PERH], strip_kind[G::PERH];
+#pragma unroll
+  for (int r = 0; r < G::PERH; ++r) {
+    const int h = tid + r * NT;
+    strip_e[r] = 0;
+    strip_kind[r] = 0;
+    if (h < G::HXU) {
+      constexpr int per_side = 2 / NP;
+      const int row = h / (2 * per_side), q = h % (2 * per_side);
+      const int rx = q < per_side ? q * NP : TX + 2 + (q - per_side) * NP;
+      strip_e[r] = (2 + row) * RX + rx;
+      strip_kind[r] = 1;
+    } else if (h < G::HU) {
+      const int hy = h - G::HXU;
+      const int rowsel = hy / TXU, col = hy % TXU;
+      const int ry = rowsel < 2 ? rowsel : TY + rowsel;  // 0,1,TY+2,TY+3
+      strip_e[r] = ry * RX + 2 + col * NP;
+      strip_kind[r] = 2;
+    }
+  }
+
   prefetch(zbase);
   cp_async_commit();
-  for (int zl = zbase; zl < z1 + 2; ++zl) {
-    const int slot = (zl - zbase) % NSLOT;
+  int slot = 0;  // ring slot of plane zl: (zl - zbase) mod NSLOT
+  for (int zl = zbase; zl < z1 + 2; ++zl, slot = (slot + 1 == NSLOT ? 0 : slot + 1)) {
     cp_async_wait<0>();
     commit(slot, zl);
     __syncthreads();
@@ -433,9 +482,12 @@ __device__ __forceinline__ void stage_tile(const Problem& P, const StageArgs& S,
     cp_async_commit();
 
     const int k = zl - 2;
-    const TC* pk[5];  // ring planes k-2 .. k+2
+    const TC* pk[5];  // ring planes k-2 .. k+2 = zl-4 .. zl: slots slot+1 .. slot+5 (mod NSLOT)
 #pragma unroll
-    for (int d = 0; d < 5; ++d) pk[d] = ring + ((zl - 4 + d - zbase + 2 * NSLOT) % NSLOT) * NFLD * PL;
+    for (int d = 0; d < 5; ++d) {
+      const int sd = slot + 1 + d;
+      pk[d] = ring + (sd >= NSLOT ? sd - NSLOT : sd) * NFLD * PL;
+    }
     TC* st = strips;
 
     // ---- phase A: s_z of plane zl (own unit, kept in registers) ...
@@ -452,19 +504,20 @@ __device__ __forceinline__ void stage_tile(const Problem& P, const StageArgs& S,
     // and every z-direction term of the own unit (its z taps of u, v, w are
     // shared with the strips).  The partial sums stay in registers across the
     // barrier and phase B adds the x and y directions.
-    V fc[5], uc[3], h0c = zero, div = zero;
-    V fcc[5];     // rho phi of the convective split (KEEP: rho e in place of rho E)
-    V pc = zero;  // centre pressure (KEEP)
+    // Per-unit values of the centre plane.  Phase A assigns each of them (the
+    // z-direction terms are the first contribution to every sum, so no sum
+    // starts from a zero fill); phase B runs only where phase A did.
+    V fc[5], uc[3], h0c, div;
+    V fcc[5];  // rho phi of the convective split (KEEP: rho e in place of rho E)
+    V pc;      // centre pressure (KEEP)
     V suf[5], udf[5], d2u[3], ds[3], kx[5];
-    V d2h = zero, dus = zero;
+    V d2h, dus;
     V grad[3][3];  // grad[i][j] = raw D_j u_i (diagnostics)
     Taps<V> ux_c, uy_c, vy_c;  // x taps of u, y taps of u and v: phase A loads them, phase B reuses
+    if constexpr (XTRA) {
 #pragma unroll
-    for (int c = 0; c < 5; ++c) {
-      suf[c] = zero; udf[c] = zero; fc[c] = zero; kx[c] = zero; fcc[c] = zero;
+      for (int c = 0; c < 5; ++c) kx[c] = zero;
     }
-#pragma unroll
-    for (int i = 0; i < 3; ++i) { d2u[i] = zero; ds[i] = zero; uc[i] = zero; }
     if (k >= z0) {
       const TC* P0 = pk[2];
       auto ztw = [&](int fld, int e) -> Taps<V> {
@@ -523,14 +576,14 @@ __device__ __forceinline__ void stage_tile(const Problem& P, const StageArgs& S,
           if constexpr (KEEP) {
             if (c >= 1 && c <= 3) Fmz[c - 1] = F;
           }
-          udf[c] = fma(uc[2], dF, udf[c]);
+          udf[c] = uc[2] * dF;
           if (c == 0) continue;
           Taps<V> g;
           if (c == 3) g = tfma(aU, F, Pt);                      // a w rho w + p
           else if (c == 4 && !KEEP) g = tmul(U, taxpy(c_alpha, F, Pt));  // w (a rho E + p)
           else g = tmul(aU, F);
-          suf[c] = suf[c] + dsum(g, c_8);
-          if (c == 3) suf[0] = fma(c_alpha, dF, suf[0]);  // D_z(rho w)
+          suf[c] = dsum(g, c_8);
+          if (c == 3) suf[0] = c_alpha * dF;  // D_z(rho w)
         }
         if constexpr (XTRA) {
           const Taps<V> UZall[3] = {uz, vz, wz};
@@ -540,30 +593,26 @@ __device__ __forceinline__ void stage_tile(const Problem& P, const StageArgs& S,
         const Taps<V>* UZ[3] = {&uz, &vz, &wz};
 #pragma unroll
         for (int i = 0; i < 3; ++i) {
-          const V w8 = (i == 2) ? c_43 : c_one;
-          d2u[i] = fma(w8, d2sum(*UZ[i], uc[i], c_16, c_m30), d2u[i]);
+          const V d2 = d2sum(*UZ[i], uc[i], c_16, c_m30);
+          d2u[i] = i == 2 ? c_43 * d2 : d2;
           if constexpr (DIAG) grad[i][2] = dsum(*UZ[i], c_8);
         }
         {
           const Taps<V> H = tfma(tscale(c_nu6, U), U, ztw(F_H0, ec));
           const V Hc = fma(c_nu6 * uc[2], uc[2], h0c);
-          d2h = d2h + d2sum(H, Hc, c_16, c_m30);
+          d2h = d2sum(H, Hc, c_16, c_m30);
         }
         {
           const Taps<V> Sj = {szq[0], szq[1], szq[3], szq[4]};
           ds[2] = dsum(Sj, c_8);
-          dus = dus + dsum(tmul(U, Sj), c_8);
+          dus = dsum(tmul(U, Sj), c_8);
         }
       }
       // halo strips: x-halo units need s_x and G_x, y-halo units s_y and G_y
 #pragma unroll
       for (int r = 0; r < G::PERH; ++r) {
-        const int h = tid + r * NT;
-        if (h < G::HXU) {
-          constexpr int per_side = 2 / NP;
-          const int row = h / (2 * per_side), q = h % (2 * per_side);
-          const int rx = q < per_side ? q * NP : TX + 2 + (q - per_side) * NP;
-          const int e = (2 + row) * RX + rx;
+        const int e = strip_e[r];
+        if (strip_kind[r] == 1) {
           const V dyv = c_inv12h * dsum(yt(P0 + F_V * PL, e), c_8);
           const Taps<V> wz = ztw(F_W, e);
           const V dzw = c_inv12h * dsum(wz, c_8);
@@ -571,11 +620,7 @@ __device__ __forceinline__ void stage_tile(const Problem& P, const StageArgs& S,
           const V eyuv = dsum(tmul(yt(P0 + F_U * PL, e), yt(P0 + F_V * PL, e)), c_8);
           const V ezuw = dsum(tmul(ztw(F_U, e), wz), c_8);
           (c_2 * c_inv12h * (eyuv + ezuw)).store(st + S_GX * PL + e);
-        } else if (h < G::HU) {
-          const int hy = h - G::HXU;
-          const int rowsel = hy / TXU, col = hy % TXU;
-          const int ry = rowsel < 2 ? rowsel : TY + rowsel;  // 0,1,TY+2,TY+3
-          const int e = ry * RX + 2 + col * NP;
+        } else if (strip_kind[r] == 2) {
           V cd;
           const V dxu = c_inv12h * dsum(xt(P0 + F_U * PL, e, cd), c_8);
           const Taps<V> wz = ztw(F_W, e);
@@ -590,12 +635,20 @@ __device__ __forceinline__ void stage_tile(const Problem& P, const StageArgs& S,
     // ---- phase B: x- and y-direction terms of the own unit, assembly, epilogue
     if (k >= z0 && active_xy) {
       const TC* P0 = pk[2];
-      // the epilogue's Q_in of the own unit at plane k (see QIN_QUEUE),
-      // issued here so that its latency hides behind the x/y terms
-      if constexpr (EPI == EPI_RK && !QIN_QUEUE) {
+      // the epilogue's Q_in of the own unit at plane k (see qin_raw), issued
+      // here so that its latency hides behind the x/y terms
+      if constexpr (EPI == EPI_RK) {
+        if constexpr (RS > 1) {
+          const RawS* src = raw_plane(k);
 #pragma unroll
-        for (int c = 0; c < 5; ++c)
-          qin_q[0][c] = IO::load(q_in + (long long)k * nn + tile_off + c * n3);
+          for (int c = 0; c < 5; ++c) qin_raw[c] = src[c * PLU + tid];
+        } else {
+          if (!qin_fc) {
+#pragma unroll
+            for (int c = 0; c < 5; ++c)
+              qin_raw[c] = IO::load(q_in + (long long)(k + zg) * nn + tile_off + c * fsq);
+          }
+        }
       }
 #pragma unroll
       for (int j = 0; j < 2; ++j) {
@@ -709,7 +762,7 @@ __device__ __forceinline__ void stage_tile(const Problem& P, const StageArgs& S,
       if constexpr (EPI == EPI_RHS) {
         TC* r_out = static_cast<TC*>(S.r_out);
 #pragma unroll
-        for (int c = 0; c < 5; ++c) R[c].store(r_out + o + c * n3);
+        for (int c = 0; c < 5; ++c) R[c].store(r_out + o + c * fst);
       } else {
         TS* q_out = static_cast<TS*>(S.q_out);
         TT* qt = static_cast<TT*>(S.qt);
@@ -720,7 +773,19 @@ __device__ __forceinline__ void stage_tile(const Problem& P, const StageArgs& S,
 #pragma unroll
         for (int c = 0; c < 5; ++c) {
           TA qtn[NP], qo[NP], qin[NP], qold[NP];
-          raw_elems<TA, NP>(qin_q[QIN_QUEUE ? 2 : 0][c], qin);
+          if constexpr (QIN_FC) {
+            if (qin_fc) {
+              if (c == 3) raw_elems<TA, NP>(qw_q[2], qin);
+              else {
+#pragma unroll
+                for (int e = 0; e < NP; ++e) qin[e] = cvt<TA>(fc[c].get(e));
+              }
+            } else {
+              raw_elems<TA, NP>(qin_raw[c], qin);
+            }
+          } else {
+            raw_elems<TA, NP>(qin_raw[c], qin);
+          }
           if (S.read_qt) raw_elems<TA, NP>(qts[c * NT + tid], qold);
 #pragma unroll
           for (int e = 0; e < NP; ++e) {
@@ -738,8 +803,8 @@ __device__ __forceinline__ void stage_tile(const Problem& P, const StageArgs& S,
               qo[e] = fma_rn(b, v, qin[e]);
             }
           }
-          UnitStore<TS, NP>::put(q_out + o + c * n3, qo);
-          if (S.write_qt) UnitStore<TT, NP>::put(qt + o + c * n3, qtn);
+          UnitStore<TS, NP>::put(q_out + o + zg * nn + c * fsq, qo);
+          if (S.write_qt) UnitStore<TT, NP>::put(qt + o + c * fst, qtn);
         }
       }
     }
@@ -763,9 +828,17 @@ __device__ __forceinline__ void stage_tile(const Problem& P, const StageArgs& S,
   }
 }
 
+// Resident CTAs per SM the register allocation targets: two for FP16
+// arithmetic (128 registers per thread; its shared memory allows two CTAs,
+// and 16 warps per SM run the pure-half stage about 20% faster than 8),
+// otherwise one (the FP32/FP64 ring allows one CTA per SM).
+template <class TC> constexpr int stage_min_blocks() {
+  return std::is_same<TC, __half>::value ? 2 : 1;
+}
+
 template <class TS, class TT, class TC, class TA, int TX, int TY, int NP, int EPI, bool DIAG,
           int SPL = SPL_QUAD>
-__global__ void __launch_bounds__(Geo<TX, TY, NP>::NT, 1)
+__global__ void __launch_bounds__(Geo<TX, TY, NP>::NT, stage_min_blocks<TC>())
 stage_kernel(const Problem P, const StageArgs S) {
   const long long cta = ((long long)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
   stage_tile<TS, TT, TC, TA, TX, TY, NP, EPI, DIAG, SPL>(P, S, blockIdx.x * TX, blockIdx.y * TY,
