@@ -71,6 +71,9 @@ def parse():
     ap.add_argument("--accuracy-workload", default="tgv", choices=["tgv", "tgsym"],
                     help="tgv: periodic 2 pi box, M 0.1, Re 1600, dt 0.00125 at 256^3; tgsym: "
                          "the symmetric pi box of Sec. 4.1/4.3, M 0.5, Re 800, dt 0.0025")
+    ap.add_argument("--probe-peaks", action="store_true",
+                    help="measure the FMA pipe in its three arithmetic forms (scalar FP32, "
+                         "paired FP32, packed FP16) with the library's probe; prints one JSON")
     ap.add_argument("--profile-case", default=None, metavar="MODE",
                     help="run 2 warm-up RK3 steps and 1 more step of MODE at --n, then exit "
                          "(the small case an ncu capture of the stage kernel uses)")
@@ -465,8 +468,11 @@ def run_ours(args, rank, world, local):
         sms = torch.cuda.get_device_properties(dev).multi_processor_count
         peak_alu = fp32_peak_tflops(sms, peaks.get("sm_max_mhz", 2032.0))
         ach_alu = flops_pp * n ** 3 / (stage_ms * 1e-3) / 1e12
+        ffma2 = tgv.probe_fma_tflops("ffma2")
         roof_alu = {"bound": "alu", "achieved": round(ach_alu, 2), "peak": round(peak_alu, 2),
                     "unit": "TFLOP/s", "frac": round(ach_alu / peak_alu, 4),
+                    "peak_measured_ffma2": round(ffma2, 2),
+                    "frac_of_measured": round(ach_alu / ffma2, 4),
                     "flops_per_point_stage": flops_pp,
                     "flops_source": "profiles/op_tally.md: the oracle's formulas, each distinct "
                                     "operation counted once (tests/op_tally.py)",
@@ -822,8 +828,23 @@ def run_reference(args, rank, world):
     return {"value": value, "ms_per_step": el * 1e3 / K, "sample": sample, "cores": cores}
 
 
+def probe_peaks():
+    import torch
+    import paper_2505_20911_b300 as tgv
+    out = {k: tgv.probe_fma_tflops(k) for k in ("ffma", "ffma2", "hfma2")}
+    props = torch.cuda.get_device_properties(0)
+    peaks, _ = measured_peaks()
+    out["derived_fp32_fma_peak"] = fp32_peak_tflops(props.multi_processor_count,
+                                                    peaks.get("sm_max_mhz", 2032.0))
+    out["unit"] = "TFLOP/s"
+    return out
+
+
 def main():
     args = parse()
+    if args.probe_peaks:
+        print(json.dumps(probe_peaks()), flush=True)
+        return
     if args.profile_case:
         profile_case(args)
         return

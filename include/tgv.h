@@ -64,9 +64,9 @@ typedef enum {
  * energy, KGP of the internal energy, the kinetic-energy split of the
  * two-point flux rho_bar u_bar (u_i u_i)~/2 and the pressure work
  * u_j D_j p + p D_j u_j; the paper cites it without printing it).
- * Feiereisen, KGP and KEEP are built for the FP64, FP32 and Q FP32 / Qt FP16
- * modes of rk_step/rhs_eval (TGV_ERR_UNSUPPORTED elsewhere, in the adjoint
- * and in the ensemble). */
+ * Every split is built for every precision mode of rk_step, rk_substep,
+ * rhs_eval and the slab stage; Feiereisen, KGP and KEEP return
+ * TGV_ERR_UNSUPPORTED in the adjoint and in the ensemble. */
 typedef enum {
   TGV_SPLIT_BLAISDELL = 0,
   TGV_SPLIT_DIVERGENCE = 1,
@@ -291,7 +291,9 @@ int32_t tgv_ensemble_destroy(tgv_ensemble* ens);
  * the state).  The paper has no counterpart; this is a library convenience.
  * q: device, Q layout; out_dev: device, double[TGV_DIAG_COUNT].
  * The first call on a device looks up the array's address (cudaGetSymbolAddress)
- * with that device current; make that first call before any stream capture.
+ * with that device current and caches it with the device's CUDA context; make
+ * that first call before any stream capture.  A call in another context (after
+ * a device reset, which recreates the context) looks the address up again.
  * All calls share the array: calls whose work overlaps on the GPU (other
  * streams, other host threads) race and must be serialised by the caller.
  * Allocates nothing; returns TGV_ERR_ARG if a problem needed more partials
@@ -403,6 +405,22 @@ int32_t tgv_slab_substep(const tgv_config* cfg, const tgv_slab* slab, const void
  */
 int32_t tgv_slab_exchange_local(const tgv_config* cfg, int32_t count, const tgv_slab* slabs,
                                 void* const* q, void* stream);
+
+/*
+ * Measurement support (no paper counterpart): throughput probe of the FMA
+ * pipe in the three arithmetic forms the stage kernels use, for the ALU
+ * roofline and the choice between FP32 pairs and packed FP16.  Launches
+ * `blocks` blocks of 256 threads on `stream`; every thread runs 8
+ * independent chains of x <- x*a + b for `iters` iterations and writes one
+ * float to sink (device, at least blocks*256 floats).  *flops (host) receives
+ * the floating-point operations the launch performs (2 per lane per FMA); the
+ * caller times the launch.  TGV_ERR_ARG on a bad argument.
+ */
+#define TGV_PROBE_FFMA 0   /* scalar FP32 fused multiply-add            */
+#define TGV_PROBE_FFMA2 1  /* paired FP32 (two lanes per instruction)   */
+#define TGV_PROBE_HFMA2 2  /* packed FP16 (half2, two lanes)            */
+int32_t tgv_probe_fma(int32_t kind, int32_t iters, int32_t blocks, float* sink,
+                      size_t sink_floats, double* flops, void* stream);
 
 #ifdef __cplusplus
 }

@@ -359,6 +359,33 @@ def tgv_slab_exchange_local(cfg: Config, slabs, qs, stream=None) -> None:
           "tgv_slab_exchange_local")
 
 
+# -------------------------------------------------------------- measurement
+PROBE_KINDS = {"ffma": 0, "ffma2": 1, "hfma2": 2}
+
+
+def probe_fma_tflops(kind: str, iters: int = 4096, blocks_per_sm: int = 8, reps: int = 5) -> float:
+    """Throughput of the FMA pipe in one arithmetic form (scalar FP32, paired
+    FP32, packed FP16), TFLOP/s: the best of `reps` timed launches of the
+    library's probe kernel (tgv_probe_fma) on the current device."""
+    dev = torch.cuda.current_device()
+    blocks = blocks_per_sm * torch.cuda.get_device_properties(dev).multi_processor_count
+    sink = torch.empty(blocks * 256, dtype=torch.float32, device="cuda")
+    flops = C.c_double(0.0)
+    stream = torch.cuda.current_stream()
+    best = None
+    for r in range(reps + 1):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        check(lib().tgv_probe_fma(PROBE_KINDS[kind], int(iters), blocks, _dev(sink, "sink"),
+                                  sink.numel(), C.byref(flops), _stream(stream)), "tgv_probe_fma")
+        e1.record(stream)
+        e1.synchronize()
+        if r:  # the first launch is a warm-up
+            t = flops.value / (e0.elapsed_time(e1) * 1e-3) / 1e12
+            best = t if best is None else max(best, t)
+    return best
+
+
 def diagnostics(cfg: Config, q: torch.Tensor, workspace=None) -> dict:
     """Convenience: diagnostics_reduce into a fresh tensor, returned as a dict."""
     ws = workspace if workspace is not None else empty_workspace(cfg, q.device)

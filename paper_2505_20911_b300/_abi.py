@@ -89,6 +89,8 @@ SIGNATURES = {
     "tgv_slab_substep": (C.c_int32, [_CFG, _SLAB, _P, _P, _P, C.c_int32, C.c_double, _P, _P,
                                      C.c_size_t, _P]),
     "tgv_slab_exchange_local": (C.c_int32, [_CFG, C.c_int32, _SLAB, C.POINTER(C.c_void_p), _P]),
+    "tgv_probe_fma": (C.c_int32, [C.c_int32, C.c_int32, C.c_int32, _P, C.c_size_t,
+                                  C.POINTER(C.c_double), _P]),
     "tgv_run_host_workspace_bytes": (C.c_size_t, [_CFG, C.c_int32, C.c_int32]),
     "tgv_run_host": (C.c_int32, [_CFG, _P, _P, C.c_double, C.c_int32, C.c_int32, _P, _P,
                                  C.c_size_t, _P]),

@@ -397,6 +397,7 @@ int32_t tgv_grad_final_ke(const tgv_config* cfg, const void* q0, double dt, int3
   auto slot = [&](int m) -> void* { return seg + (size_t)m * qb; };
 
   // forward with checkpoints Q_0, Q_c, Q_2c, ... (seg slots 0/1 as ping-pong)
+  NvtxRange fwd_range("tgv adjoint: forward with checkpoints");
   TGV_CUDA_TRY(cudaMemcpyAsync(slot(0), q0, qraw, cudaMemcpyDeviceToDevice, st));
   int cur = 0;
   for (int m = 0; m < nsteps; ++m) {
@@ -423,6 +424,7 @@ int32_t tgv_grad_final_ke(const tgv_config* cfg, const void* q0, double dt, int3
   // reverse sweep, one checkpoint segment at a time: recompute the segment
   // keeping every stage input, then run the step adjoints backwards
   for (int sgi = nck - 1; sgi >= 0; --sgi) {
+    NvtxRange seg_range("tgv adjoint: segment recompute + reverse");
     const int m0 = sgi * ckpt_every;
     const int m1 = (m0 + ckpt_every < nsteps) ? m0 + ckpt_every : nsteps;
     TGV_CUDA_TRY(cudaMemcpyAsync(slot(0), ckpt + (size_t)sgi * qb, qraw, cudaMemcpyDeviceToDevice, st));

@@ -11,6 +11,8 @@
 
 namespace tgv {
 
+static const char* const STAGE_NAMES[3] = {"tgv stage 1", "tgv stage 2", "tgv stage 3"};
+
 const ModeLaunchers& mode_launchers_0();
 const ModeLaunchers& mode_launchers_1();
 const ModeLaunchers& mode_launchers_2();
@@ -60,7 +62,7 @@ Problem make_problem(const tgv_config& c) {
   return P;
 }
 
-static int find_mode(const tgv_config& c) {
+int find_mode(const tgv_config& c) {
   for (int m = 0; m < NUM_MODES; ++m) {
     const ModeKey& k = MODE_KEYS[m];
     if (k.qs == c.q_storage && k.qts == c.qt_storage && k.comp == c.compute && k.acc == c.accumulate)
@@ -352,7 +354,9 @@ int32_t rk_step(const tgv_config* cfg, void* q_a, void* q_b, void* qt, double dt
   const Problem P = make_problem(*cfg);
   for (int32_t m = 0; m < nsteps; ++m) {
     const bool log = diag_every > 0 && m % diag_every == 0;
+    NvtxRange step_range("tgv rk_step");
     for (int i = 0; i < 3; ++i) {
+      NvtxRange stage_range(STAGE_NAMES[i]);
       // the first substep of a logged step also reduces the diagnostics of Q^m
       long long ctas = 0;
       double* part = (log && i == 0) ? static_cast<double*>(workspace) : nullptr;
@@ -575,6 +579,7 @@ int32_t tgv_slab_substep(const tgv_config* cfg, const tgv_slab* slab, const void
   S.fs_q = slab_fs(cfg, slab);
   S.fs_t = (long long)slab->nz * cfg->n * cfg->n;
   long long ctas = 0;
+  NvtxRange stage_range(STAGE_NAMES[i]);
   s = launch_stage_common(cfg, S, false, (cudaStream_t)stream, &ctas);
   if (s != TGV_OK) return s;
   if (diag_dev) {
@@ -601,6 +606,7 @@ int32_t tgv_slab_exchange_local(const tgv_config* cfg, int32_t count, const tgv_
   const size_t es = dtype_size(cfg->q_storage);
   const size_t nn = (size_t)cfg->n * cfg->n, blk = 2 * nn * es;
   cudaStream_t st = (cudaStream_t)stream;
+  NvtxRange range("tgv slab ghost exchange");
   for (int32_t r = 0; r < count; ++r) {
     const int32_t lo = (r + count - 1) % count, hi = (r + 1) % count;
     char* dst = static_cast<char*>(q[r]);

@@ -10,9 +10,21 @@
 #include <cuda_bf16.h>
 #include <stdint.h>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "tgv.h"
 
 namespace tgv {
+
+// NVTX range for profilers (a no-op unless a tool is attached): the RK steps,
+// stages, adjoint sweeps and ensemble replays the library enqueues are named
+// in a timeline.
+struct NvtxRange {
+  explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+  NvtxRange(const NvtxRange&) = delete;
+  NvtxRange& operator=(const NvtxRange&) = delete;
+};
 
 // ---------------------------------------------------------------- conversions
 template <class T> struct Num;

@@ -283,6 +283,7 @@ int32_t tgv_ensemble_create(const tgv_config* cfgs, int32_t count, void* const* 
 
 int32_t tgv_ensemble_run(tgv_ensemble* E, int32_t replays, void* stream) {
   if (!E || replays < 0) return TGV_ERR_ARG;
+  NvtxRange range("tgv ensemble replays");
   for (int r = 0; r < replays; ++r)
     if (cudaGraphLaunch(E->exec, static_cast<cudaStream_t>(stream)) != cudaSuccess)
       return TGV_ERR_CUDA;

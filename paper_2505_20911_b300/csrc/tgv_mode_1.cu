@@ -8,7 +8,7 @@ const ModeLaunchers& mode_launchers_1() {
   // CTA per SM; two 16x16 CTAs per SM overlap one CTA's FP64 epilogue with
   // the other's FP32 stencil work and measured about 10% faster at 256^3.
   static const ModeLaunchers L = [] {
-    ModeLaunchers m = make_launchers<double, double, float, double>();
+    ModeLaunchers m = make_launchers<double, double, float, double, true>();
     m.first_tile = 1;
     return m;
   }();

@@ -4,7 +4,7 @@
 
 namespace tgv {
 const ModeLaunchers& mode_launchers_2() {
-  static const ModeLaunchers L = make_launchers<float, float, double, double>();
+  static const ModeLaunchers L = make_launchers<float, float, double, double, true>();
   return L;
 }
 }  // namespace tgv

@@ -4,7 +4,7 @@
 
 namespace tgv {
 const ModeLaunchers& mode_launchers_4() {
-  static const ModeLaunchers L = make_launchers<__nv_bfloat16, __nv_bfloat16, float, float>();
+  static const ModeLaunchers L = make_launchers<__nv_bfloat16, __nv_bfloat16, float, float, true>();
   return L;
 }
 }  // namespace tgv

@@ -4,7 +4,7 @@
 
 namespace tgv {
 const ModeLaunchers& mode_launchers_5() {
-  static const ModeLaunchers L = make_launchers<__half, __half, float, float>();
+  static const ModeLaunchers L = make_launchers<__half, __half, float, float, true>();
   return L;
 }
 }  // namespace tgv

@@ -4,7 +4,7 @@
 
 namespace tgv {
 const ModeLaunchers& mode_launchers_6() {
-  static const ModeLaunchers L = make_launchers<__half, __half, __half, float>();
+  static const ModeLaunchers L = make_launchers<__half, __half, __half, float, true>();
   return L;
 }
 }  // namespace tgv

@@ -61,6 +61,9 @@ struct ModeLaunchers {
 };
 
 const ModeLaunchers& mode_launchers(int mode);
+// Index into MODE_KEYS of a config's (q_storage, qt_storage, compute,
+// accumulate), or -1 if that combination is not built.
+int find_mode(const tgv_config& c);
 
 template <class TS, class TT, class TC, class TA, int TX, int TY, int NP, int EPI, bool DIAG,
           int SPL = SPL_QUAD>

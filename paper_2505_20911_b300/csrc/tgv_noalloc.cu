@@ -11,10 +11,15 @@
 //
 // The array lives for the lifetime of the process on every device that loads
 // the library (NOALLOC_PARTIALS doubles, about 95 KB).  Host code cannot use
-// its name as a device address, so the first call on each device looks the
-// address up with cudaGetSymbolAddress (with that device current) and caches
-// it; that first call should therefore come before any stream capture.
-#include <atomic>
+// its name as a device address, so a call looks the address up with
+// cudaGetSymbolAddress (with the device current) and caches it per device
+// together with the CUDA context it belongs to; a call in another context (a
+// device reset recreates the primary context and reloads the module) looks it
+// up again.  The first call on a device, which does the lookup, should come
+// before any stream capture.
+#include <cuda.h>  // the CUcontext type only; the driver function is obtained at run time
+
+#include <mutex>
 
 #include "tgv_modes.cuh"
 
@@ -28,26 +33,45 @@ constexpr size_t NOALLOC_PARTIALS = (size_t)NOALLOC_BLOCKS * TGV_DIAG_COUNT;
 static __device__ __align__(256) double g_noalloc_partials[NOALLOC_PARTIALS];
 
 constexpr int NOALLOC_MAX_DEVICES = 64;
-static std::atomic<double*> g_noalloc_ptr[NOALLOC_MAX_DEVICES];
+struct NoallocCache {
+  CUcontext ctx;
+  double* ptr;
+};
+static NoallocCache g_noalloc_cache[NOALLOC_MAX_DEVICES];
+static std::mutex g_noalloc_mutex;
 
-// Device address of the partials array on the current device (looked up once).
-static double* noalloc_scratch(int dev) {
-  double* p = g_noalloc_ptr[dev].load(std::memory_order_acquire);
-  if (p) return p;
-  void* addr = nullptr;
-  if (cudaGetSymbolAddress(&addr, g_noalloc_partials) != cudaSuccess || !addr) return nullptr;
-  p = static_cast<double*>(addr);
-  g_noalloc_ptr[dev].store(p, std::memory_order_release);
-  return p;
+// cuCtxGetCurrent through the runtime's driver entry-point query (null if the
+// driver does not provide it; the cache then keys on the device alone).
+using CtxGetCurrentFn = CUresult (*)(CUcontext*);
+static CtxGetCurrentFn ctx_get_current() {
+  static const CtxGetCurrentFn fn = [] {
+    void* f = nullptr;
+    cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 2000, cudaEnableDefault, &q) !=
+            cudaSuccess || q != cudaDriverEntryPointSuccess)
+      f = nullptr;
+    return reinterpret_cast<CtxGetCurrentFn>(f);
+  }();
+  return fn;
 }
 
-static int noalloc_mode(const tgv_config& c) {
-  for (int m = 0; m < NUM_MODES; ++m) {
-    const ModeKey& k = MODE_KEYS[m];
-    if (k.qs == c.q_storage && k.qts == c.qt_storage && k.comp == c.compute && k.acc == c.accumulate)
-      return m;
-  }
-  return -1;
+static CUcontext current_ctx() {
+  CUcontext ctx = nullptr;
+  const CtxGetCurrentFn fn = ctx_get_current();
+  if (fn && fn(&ctx) != CUDA_SUCCESS) ctx = nullptr;
+  return ctx;
+}
+
+// Device address of the partials array on the current device and context.
+static double* noalloc_scratch(int dev) {
+  std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+  NoallocCache& c = g_noalloc_cache[dev];
+  if (c.ptr && c.ctx == current_ctx()) return c.ptr;
+  void* addr = nullptr;
+  if (cudaGetSymbolAddress(&addr, g_noalloc_partials) != cudaSuccess || !addr) return nullptr;
+  c.ptr = static_cast<double*>(addr);
+  c.ctx = current_ctx();  // the lookup has made the device's context current
+  return c.ptr;
 }
 
 }  // namespace tgv
@@ -72,7 +96,7 @@ extern "C" int32_t diagnostics_reduce_noalloc(const tgv_config* cfg, const void*
   // so nothing in the array has to be cleared beforehand.
   const Problem P = make_problem(*cfg);
   cudaStream_t st = static_cast<cudaStream_t>(stream);
-  if (mode_launchers(noalloc_mode(*cfg)).diag_partial(P, q, part, (int)nb, st) != cudaSuccess)
+  if (mode_launchers(find_mode(*cfg)).diag_partial(P, q, part, (int)nb, st) != cudaSuccess)
     return TGV_ERR_CUDA;
   diag_final_kernel<<<1, 32 * TGV_DIAG_COUNT, 0, st>>>(P, part, (int)nb, out_dev);
   if (cudaGetLastError() != cudaSuccess) return TGV_ERR_CUDA;

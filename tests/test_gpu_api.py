@@ -93,3 +93,28 @@ def test_workspace_errors():
         tgv.rk_step(cfg, q, qb, qt, 0.05, 1)           # above the stability limit
     assert ei.value.status == _abi.TGV_ERR_UNSTABLE_DT
     tgv.rk_step(cfg.with_(allow_unstable_dt=True), q, qb, qt, 0.02, 1)  # allowed when asked
+
+
+def test_resume_from_a_checkpoint_is_bit_exact(tmp_path):
+    """6 steps in one go equal 3 steps, save, load, 3 more steps (the RK
+    increment restarts every step, so Q alone carries the run)."""
+    import os
+    from paper_2505_20911_b300 import checkpoint
+    cfg = tgv.Config(n=32, mode="hpsp")
+    dt = 0.004
+    qa = tgv.empty_state(cfg)
+    tgv.tgv_init(cfg, qa)
+    q0 = qa.clone()
+    qb, qt = torch.empty_like(qa), tgv.empty_qt(cfg)
+    par = tgv.rk_step(cfg, qa, qb, qt, dt, 6)
+    straight = (qb if par else qa).clone()
+    qa.copy_(q0)
+    par = tgv.rk_step(cfg, qa, qb, qt, dt, 3)
+    path = os.path.join(tmp_path, "mid.tgvq")
+    checkpoint.save_state(path, cfg, qb if par else qa, step=3, time=3 * dt)
+    cfg2, q3, step, t = checkpoint.load_state(path)
+    assert cfg2 == cfg and step == 3
+    qa2 = q3.contiguous()
+    qb2, qt2 = torch.empty_like(qa2), tgv.empty_qt(cfg2)
+    par = tgv.rk_step(cfg2, qa2, qb2, qt2, dt, 3)
+    assert torch.equal(qb2 if par else qa2, straight)

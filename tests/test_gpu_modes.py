@@ -31,7 +31,8 @@ DISS_TARGET = 1e-2
 #     test also asserts DISS_TARGET itself.
 #   kind "measured": the mode does not meet DISS_TARGET (Q stored in 16 bits);
 #     its bounds are a regression band of about 3x the errors measured on a
-#     B300 at this size, not the target.
+#     B300 at this size, not the target (measured: bf16_fp32 fields 8.1e-2,
+#     dissipation 1.26; fp16_fp32 2.3e-2, 3.34; fp16 4.1e-2, 0.81).
 #   FP32-class arithmetic and Q storage (u = 6e-8): about STEPS * 3 roundings
 #     of Q whose effect on the momentum is amplified by the pressure-dominated
 #     flux sums (|rho E + p| / |R| ~ 1e2): fields ~1e-5, dissipation rate
@@ -46,9 +47,9 @@ MODES = {
     "fp32s_fp64c": ("plain", 2e-5, 5e-4, "target"),
     "fp32": ("plain", 2e-5, 5e-4, "target"),
     "hpsp": ("plain", 2e-5, 5e-4, "target"),
-    "bf16_fp32": ("offset", 2e-1, None, "measured"),
-    "fp16_fp32": ("offset", 5e-2, None, "measured"),
-    "fp16": ("offset", 1e-1, None, "measured"),
+    "bf16_fp32": ("offset", 2.5e-1, 4.0, "measured"),
+    "fp16_fp32": ("offset", 7e-2, 10.0, "measured"),
+    "fp16": ("offset", 1.2e-1, 2.5, "measured"),
 }
 
 

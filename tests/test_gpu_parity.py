@@ -107,8 +107,10 @@ def test_diagnostics_match_oracle_on_random_state():
     q64 = random_state(cfg, seed=5)
     q64[1, 3, 4, 5] = float("nan")
     q64[4, 7, 7, 7] = float("inf")
+    q64[0, 7, 7, 7] = float("-inf")       # a second bad component at the same point
     got = tgv.diagnostics(cfg, encode(cfg, q64))
-    assert got["nonfinite"] == 2.0
+    assert got["nonfinite"] == oracle.diagnostics(oracle_flow(cfg), q64)["nonfinite"] == 2.0
+    q64[0, 7, 7, 7] = 1.0
     q64[1, 3, 4, 5] = 0.1
     q64[4, 7, 7, 7] = 50.0
     got = tgv.diagnostics(cfg, encode(cfg, q64))
@@ -264,24 +266,42 @@ def test_study_splits_rhs_and_steps_match_oracle(n, tile, split):
 
 
 @pytest.mark.parametrize("split", ["feiereisen", "kgp", "keep"])
-def test_study_splits_unsupported_where_not_built(split):
-    cfg = tgv.Config(n=32, mode="fp16_fp32", split=split)
+def test_study_splits_unsupported_in_the_adjoint_and_the_ensemble(split):
+    cfg = tgv.Config(n=32, mode="fp64", split=split)
     q = tgv.empty_state(cfg)
-    r = torch.empty(5, 32, 32, 32, dtype=torch.float32, device="cuda")
+    tgv.tgv_init(cfg, q)
+    lam = torch.zeros(5, 32, 32, 32, dtype=torch.float64, device="cuda")
     with pytest.raises(tgv.TGVError) as ei:
-        tgv.rhs_eval(cfg, q, r)
+        tgv.rhs_vjp(cfg, q, lam, torch.empty_like(lam))
     assert ei.value.status == tgv._abi.TGV_ERR_UNSUPPORTED
+    c32 = cfg.with_(mode="fp32")
+    qa = tgv.empty_state(c32)
+    with pytest.raises(tgv.TGVError) as ei:
+        tgv.Ensemble([c32], [qa], [torch.empty_like(qa)], [tgv.empty_qt(c32)], [0.004])
+    assert ei.value.status in (tgv._abi.TGV_ERR_UNSUPPORTED, tgv._abi.TGV_ERR_ARG)
+
+
+# mode -> bound on max |R - R_oracle| / max |R_oracle| per field, the oracle
+# evaluated on the decoded stored state (so only the arithmetic differs):
+# FP32 arithmetic 5e-6 (about 80 units of FP32 rounding; measured 2-3e-7),
+# FP64 arithmetic 1e-11 (measured 6e-16), FP16 arithmetic 1e-2 (about 20 units
+# of FP16 rounding; measured 2.2e-3).
+STUDY_MODES = {"fp32": 5e-6, "hpsp": 5e-6, "spdp": 5e-6, "fp32s_fp64c": 1e-11,
+               "bf16_fp32": 5e-6, "fp16_fp32": 5e-6, "fp16": 1e-2}
 
 
 @pytest.mark.parametrize("split", ["feiereisen", "kgp", "keep"])
-@pytest.mark.parametrize("mode", ["fp32", "hpsp"])
-def test_study_splits_reduced_precision_rhs(mode, split):
-    """The study's split forms in its FP32-compute modes: the residual on a
-    random state within FP32 rounding of the oracle (2e-4 of each field's
-    largest value, as for the quadratic forms at this Mach number)."""
-    cfg = tgv.Config(n=32, mode=mode, split=split, mach=0.3, re=100.0)
+@pytest.mark.parametrize("mode", list(STUDY_MODES))
+def test_study_splits_every_mode_rhs(mode, split):
+    """The study's split forms in every precision mode: the residual on a
+    random state against the oracle's on the same (decoded) stored state."""
+    enc = "offset" if mode in ("bf16_fp32", "fp16_fp32", "fp16") else "plain"
+    cfg = tgv.Config(n=32, mode=mode, split=split, mach=0.3, re=100.0, encoding=enc)
     q64 = random_state(cfg, seed=29)
-    r = torch.empty(5, 32, 32, 32, dtype=torch.float32, device="cuda")
-    tgv.rhs_eval(cfg, encode(cfg, q64), r)
-    ref = oracle.residual(oracle_flow(cfg), decode(cfg, encode(cfg, q64)))
-    assert max(max_rel(r.double().cpu(), ref)) < 2e-4
+    qs = encode(cfg, q64)
+    r = torch.empty(5, 32, 32, 32, dtype=cfg.compute_dtype, device="cuda")
+    tgv.rhs_eval(cfg, qs, r)
+    ref = oracle.residual(oracle_flow(cfg), decode(cfg, qs))
+    err = max(max_rel(r.double().cpu(), ref))
+    print(f"\n{mode:12s} {split:10s} max field error {err:.2e}")
+    assert err < STUDY_MODES[mode], err

@@ -101,3 +101,17 @@ def test_symmetries_persist_over_steps():
         q = oracle.rk3_step(flow, q, 0.004)
     for op in _tgv_symmetry_ops(16):
         assert torch.allclose(op(q), q, rtol=0, atol=1e-12 * float(q.abs().max()))
+
+
+def test_nonfinite_count_counts_points_not_components():
+    """The oracle's non-finite diagnostic is the number of grid points where
+    any of the 5 components is NaN or +-Inf: plant 4 bad values at 3 points
+    (two components at one point) and 1 huge finite value."""
+    flow = oracle.Flow(n=8)
+    q = oracle.initial_condition(flow)
+    q[0, 1, 2, 3] = float("nan")
+    q[4, 1, 2, 3] = float("inf")          # same point as the NaN
+    q[2, 5, 0, 7] = float("-inf")
+    q[3, 7, 7, 0] = float("nan")
+    q[1, 0, 0, 0] = 1e300                 # finite
+    assert oracle.diagnostics(flow, q)["nonfinite"] == 3.0
