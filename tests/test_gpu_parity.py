@@ -247,6 +247,55 @@ def test_full_size_rk_step_sampled(mode):
         assert exact >= 0.7 * total, (exact, total)
 
 
+def test_full_size_rk_step_sampled_headline_hpsp():
+    """The benchmark's headline configuration end to end: one full rk_step at
+    256^3 in the HPSP mode (Q FP32, the increment stored in FP16, kept divided
+    by dt), at sampled points, against the oracle step on a 16^3 periodic
+    window with Q rounded to FP32 and the increment to FP16 where rk_step
+    stores them.  FP32 against FP64 arithmetic in the residual may flip the
+    FP16 rounding of a stored increment (one FP16 ulp, 2^-11 of it), which the
+    stage weight B dt carries into Q; bound per value: three FP32 roundings of
+    the stored value, the FP32 arithmetic term of the FP32 mode's bound, and
+    one FP16 ulp of the largest stored increment times the sum of B dt."""
+    cfg = tgv.Config(n=256, mode="hpsp")
+    dt = 0.00125
+    qa = tgv.empty_state(cfg)
+    qb, qt = torch.empty_like(qa), tgv.empty_qt(cfg)
+    tgv.tgv_init(cfg, qa)
+    q_in = qa.clone()
+    par = tgv.rk_step(cfg, qa, qb, qt, dt, 1)
+    q_out = qb if par else qa
+    torch.cuda.synchronize()
+    wf = window_flow(cfg, half=8)
+    rng = np.random.Generator(np.random.PCG64(4343))
+    pts = [tuple(int(v) for v in rng.integers(0, cfg.n, size=3)) for _ in range(16)]
+    pts += [(0, 0, 0), (255, 255, 255), (128, 0, 255)]
+    h = cfg.length / cfg.n
+    big = 1.0 / (cfg.gamma * (cfg.gamma - 1) * cfg.mach ** 2) + 1.0 / (cfg.gamma * cfg.mach ** 2)
+    arith = 12 * dt * 2.0 ** -24 * torch.tensor([4.0, big + 4, big + 4, big + 4, big + 4],
+                                                 dtype=torch.float64) * 1.5 / h
+    worst, exact, total = 0.0, 0, 0
+    for k, j, i in pts:
+        q = decode(cfg, window(q_in, k, j, i, half=8))
+        w = torch.zeros_like(q)
+        wmax = torch.zeros(5, dtype=torch.float64)
+        for st in range(3):
+            w = oracle.RK_A[st] * w + oracle.residual(wf, q)
+            if st < 2:
+                w = w.half().double()
+            wmax = torch.maximum(wmax, w[:, 8, 8, 8].abs())
+            q = (q + oracle.RK_B[st] * dt * w).float().double()
+        ref = q[:, 8, 8, 8]
+        got = decode(cfg, q_out[:, k, j, i].reshape(5, 1, 1, 1)).reshape(5)
+        bound = (3 * 2.0 ** -24 * (ref.abs() + 1e-4) + arith
+                 + sum(oracle.RK_B) * dt * 2.0 ** -10 * wmax)
+        exact += int((got == ref).sum())
+        total += 5
+        worst = max(worst, float(((got - ref).abs() / bound).max()))
+        assert bool(((got - ref).abs() <= bound).all()), ((k, j, i), got - ref, bound)
+    print(f"\nhpsp: largest error / bound = {worst:.3f}; exact {exact} of {total}")
+
+
 @pytest.mark.parametrize("split", ["feiereisen", "kgp", "keep"])
 @pytest.mark.parametrize("n,tile", [(32, 0), (40, 0), (48, 3)])
 def test_study_splits_rhs_and_steps_match_oracle(n, tile, split):
