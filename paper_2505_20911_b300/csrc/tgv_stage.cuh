@@ -121,13 +121,13 @@ __host__ __device__ constexpr int raw_slots() {
 }
 
 // Shared memory: ring, strips (compute type), then the cp.async staging of
-// the raw planes (storage type) and two raw Qt planes of the tile.
+// the raw planes (storage type) and one raw Qt plane of the tile.
 template <class TS, class TT, class TC, int TX, int TY, int NP>
 constexpr size_t stage_smem_bytes() {
   using G = Geo<TX, TY, NP>;
   return sizeof(TC) * ((size_t)NSLOT * NFLD * G::PL + (size_t)NSTRIP * G::PL) +
          sizeof(TS) * NP * 5 * (size_t)G::PLU * raw_slots<TS, TC>() +
-         sizeof(TT) * NP * 2 * 5 * (size_t)G::NT;
+         sizeof(TT) * NP * 5 * (size_t)G::NT;
 }
 // Largest dynamic shared memory a stage CTA may request (B300: 227 KB per CTA,
 // less the static reduction buffer of the fused-diagnostics variant).
@@ -280,7 +280,7 @@ __device__ __forceinline__ void stage_tile(const Problem& P, const StageArgs& S,
   using RawT = typename UnitIO<TA, NP, TT>::Raw;
   constexpr int RS = raw_slots<TS, TC>();
   RawS* stage_q = reinterpret_cast<RawS*>(strips + NSTRIP * PL);       // [RS][5][PLU]
-  RawT* stage_t = reinterpret_cast<RawT*>(stage_q + RS * 5 * PLU);    // [2][5][NT]
+  RawT* stage_t = reinterpret_cast<RawT*>(stage_q + RS * 5 * PLU);    // [5][NT]
   const int zbase = z0 - 2;
   // staging slot of raw plane zl (RS is a power of two)
   auto raw_plane = [&](int zl) -> RawS* { return stage_q + ((zl - zbase) & (RS - 1)) * 5 * PLU; };
@@ -343,7 +343,7 @@ __device__ __forceinline__ void stage_tile(const Problem& P, const StageArgs& S,
   auto prefetch_qt = [&](int kq) {  // cp.async of this unit's Qt at plane kq
     if (!active_xy) return;
     const TT* qt = static_cast<const TT*>(S.qt);
-    RawT* dst = stage_t + (kq & 1) * 5 * NT;
+    RawT* dst = stage_t;
 #pragma unroll
     for (int c = 0; c < 5; ++c)
       cp_async<sizeof(RawT)>(dst + c * NT + tid, qt + (long long)kq * nn + tile_off + c * fst);
@@ -476,9 +476,15 @@ __device__ __forceinline__ void stage_tile(const Problem& P, const StageArgs& S,
     cp_async_wait<0>();
     commit(slot, zl);
     __syncthreads();
-    // next plane and, for the next centre plane, this unit's Qt (one group)
+    // this centre plane's Qt (its own group, which the epilogue waits for),
+    // then the next raw plane (a second group, waited for by the next
+    // iteration); one Qt staging plane suffices because every thread reads
+    // only the unit it copied, in the epilogue of this same iteration
+    if (EPI == EPI_RK && S.read_qt && zl - 2 >= z0 && zl - 2 < z1) {
+      prefetch_qt(zl - 2);
+      cp_async_commit();
+    }
     if (zl + 1 < z1 + 2) prefetch(zl + 1);
-    if (EPI == EPI_RK && S.read_qt && zl - 1 >= z0 && zl - 1 < z1) prefetch_qt(zl - 1);
     cp_async_commit();
 
     const int k = zl - 2;
@@ -768,8 +774,8 @@ __device__ __forceinline__ void stage_tile(const Problem& P, const StageArgs& S,
         TT* qt = static_cast<TT*>(S.qt);
         const TA a = cvt<TA>(S.a), b = cvt<TA>(S.b), dt = cvt<TA>(S.dt);
         const TA bdt = cvt<TA>(S.bdt);
-        if (S.read_qt) cp_async_wait<1>();  // this plane's Qt group has landed
-        const RawT* qts = stage_t + (k & 1) * 5 * NT;
+        if (S.read_qt) cp_async_wait<1>();  // all but the newest group (the next raw plane)
+        const RawT* qts = stage_t;
 #pragma unroll
         for (int c = 0; c < 5; ++c) {
           TA qtn[NP], qo[NP], qin[NP], qold[NP];
