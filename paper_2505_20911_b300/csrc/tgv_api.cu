@@ -324,8 +324,7 @@ int32_t diagnostics_reduce(const tgv_config* cfg, const void* q, double* out_dev
   if (!q || !out_dev) return TGV_ERR_ARG;
   if (!workspace || ws_bytes < tgv_workspace_bytes(cfg)) return TGV_ERR_WORKSPACE;
   const Problem P = make_problem(*cfg);
-  const long long items = (long long)((cfg->n + DIAG_TX - 1) / DIAG_TX) *
-                          ((cfg->n + DIAG_TY - 1) / DIAG_TY) * cfg->n;
+  const long long items = diag_items(cfg->n);
   const long long nb = items < DIAG_MAX_BLOCKS ? items : DIAG_MAX_BLOCKS;
   cudaStream_t st = (cudaStream_t)stream;
   double* part = static_cast<double*>(workspace);

@@ -113,10 +113,38 @@ __device__ __forceinline__ __half recip(__half v) { return hrcp(v); }
 __device__ __forceinline__ float fma_rn(float a, float b, float c) { return __fmaf_rn(a, b, c); }
 __device__ __forceinline__ double fma_rn(double a, double b, double c) { return __fma_rn(a, b, c); }
 
-template <class T> __device__ __forceinline__ bool finite_val(T v) {
-  double d = Num<T>::to_f64(v);
-  return isfinite(d);
+// Per-thread accumulators of the diagnostics.  FP64 arithmetic runs at about
+// 1/64 of the FP32 rate on B300, so in the FP32-arithmetic kernels each
+// thread sums its per-point values with compensated (Kahan) FP32 summation,
+// whose result is within about one FP32 rounding of the exact sum of its
+// terms, and converts once to FP64, where the partials of all threads are
+// added; FP64-arithmetic kernels add in FP64 directly.
+struct KahanF {
+  float s = 0.f, c = 0.f;  // running sum and its negated rounding error
+  __device__ __forceinline__ void add(float x) {
+    const float y = __fsub_rn(x, c);
+    const float t = __fadd_rn(s, y);
+    c = __fsub_rn(__fsub_rn(t, s), y);
+    s = t;
+  }
+  __device__ __forceinline__ double value() const { return (double)s - (double)c; }
+};
+struct PlainD {
+  double s = 0.0;
+  __device__ __forceinline__ void add(double x) { s += x; }
+  __device__ __forceinline__ double value() const { return s; }
+};
+template <class T> struct DiagAcc { using A = KahanF; using In = float; };
+template <> struct DiagAcc<double> { using A = PlainD; using In = double; };
+
+// Finite (neither NaN nor +-Inf): the exponent field is not all ones.
+__device__ __forceinline__ bool finite_val(float v) {
+  return (__float_as_uint(v) & 0x7F800000u) != 0x7F800000u;
 }
+__device__ __forceinline__ bool finite_val(__half v) {
+  return (__half_as_ushort(v) & 0x7C00u) != 0x7C00u;
+}
+__device__ __forceinline__ bool finite_val(double v) { return isfinite(v); }
 
 // ------------------------------------------------------------ problem params
 // Per-problem constants, precomputed on the host in FP64.

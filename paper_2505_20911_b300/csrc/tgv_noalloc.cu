@@ -83,8 +83,7 @@ extern "C" int32_t diagnostics_reduce_noalloc(const tgv_config* cfg, const void*
   const int32_t s = tgv_check_config(cfg);
   if (s != TGV_OK) return s;
   if (!q || !out_dev) return TGV_ERR_ARG;
-  const long long items = (long long)((cfg->n + DIAG_TX - 1) / DIAG_TX) *
-                          ((cfg->n + DIAG_TY - 1) / DIAG_TY) * cfg->n;
+  const long long items = diag_items(cfg->n);
   const long long nb = items < DIAG_MAX_BLOCKS ? items : DIAG_MAX_BLOCKS;
   if (nb > NOALLOC_BLOCKS) return TGV_ERR_ARG;  // more partials than the fixed array holds
   int dev = -1;

@@ -430,13 +430,12 @@ __device__ __forceinline__ void stage_tile(const Problem& P, const StageArgs& S,
     return {V::load(f + e - 2 * RX), V::load(f + e - RX), V::load(f + e + RX), V::load(f + e + 2 * RX)};
   };
 
-  // diagnostics accumulators (per thread, FP64; per-point values are formed in
-  // the compute type, the NP lanes of a unit summed, then added in FP64)
-  double dacc[TGV_DIAG_COUNT];
-  if constexpr (DIAG) {
-#pragma unroll
-    for (int m = 0; m < TGV_DIAG_COUNT; ++m) dacc[m] = 0.0;
-  }
+  // diagnostics accumulators (per thread; per-point values are formed in the
+  // compute type and the NP lanes of a unit summed, then accumulated by
+  // DiagAcc: compensated FP32 sums in the FP32/FP16 kernels, FP64 in the FP64
+  // ones; every thread's sum is added in FP64)
+  using DA = DiagAcc<TC>;
+  typename DA::A dacc[TGV_DIAG_COUNT];
 
   const int rxc = 2 + NP * tx, ryc = 2 + ty;
   const int ec = ryc * RX + rxc;        // unit centre in plane layout
@@ -751,17 +750,17 @@ __device__ __forceinline__ void stage_tile(const Problem& P, const StageArgs& S,
           TC t = vals[m].get(0);
 #pragma unroll
           for (int e = 1; e < NP; ++e) t = t + vals[m].get(e);
-          dacc[slot_of[m]] += (double)Num<TC>::to_f64(t);
+          dacc[slot_of[m]].add(cvt<typename DA::In>(t));
         }
-        double bad = 0.0;
+        int bad = 0;
 #pragma unroll
         for (int e = 0; e < NP; ++e) {
           bool ok = true;
 #pragma unroll
           for (int c = 0; c < 5; ++c) ok = ok && finite_val(fc[c].get(e));
-          bad += ok ? 0.0 : 1.0;
+          bad += ok ? 0 : 1;
         }
-        dacc[9] += bad;
+        dacc[9].add((typename DA::In)bad);
       }
 
       const long long o = (long long)k * nn + tile_off;
@@ -822,7 +821,7 @@ __device__ __forceinline__ void stage_tile(const Problem& P, const StageArgs& S,
     const int lane = tid & 31, warp = tid >> 5;
 #pragma unroll
     for (int m = 0; m < TGV_DIAG_COUNT; ++m) {
-      const double v = warp_sum(dacc[m]);
+      const double v = warp_sum(dacc[m].value());
       if (lane == 0) red[warp][m] = v;
     }
     __syncthreads();
