@@ -258,7 +258,9 @@ int32_t tgv_grad_final_ke(const tgv_config* cfg, const void* q0, double dt, int3
  * dt, advanced together by one persistent launch per RK stage over a
  * flattened list of (instance, tile, z chunk) work items, the launches of
  * steps_per_graph steps captured in a CUDA graph that tgv_ensemble_run
- * replays.  Built for the FP32 mode (all four types TGV_F32).
+ * replays.  Built for every precision mode; all instances of one ensemble
+ * share the mode (TGV_ERR_ARG otherwise) and use a quadratic split form
+ * (Blaisdell or divergence; TGV_ERR_UNSUPPORTED otherwise).
  * cfgs[i], q_a[i], q_b[i], qt[i], dts[i]: instance i (device buffers of that
  *   instance's size; q_a holds Q on entry and again after every replay,
  *   q_b and qt are scratch).  count: 1..64.  steps_per_graph: even, >= 2.

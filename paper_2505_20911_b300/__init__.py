@@ -463,9 +463,9 @@ class TGVFinalKE(torch.autograd.Function):
 
 # ------------------------------------------------------------------ ensemble
 class Ensemble:
-    """Owner of a tgv_ensemble handle: `count` FP32 TGV instances of uneven
-    size advanced together (one persistent launch per RK stage, replayed from
-    a CUDA graph of steps_per_graph steps).  Buffers are torch tensors the
+    """Owner of a tgv_ensemble handle: `count` TGV instances of uneven size,
+    all in one precision mode, advanced together (one persistent launch per RK
+    stage, replayed from a CUDA graph of steps_per_graph steps).  Buffers are torch tensors the
     caller keeps alive; q_a[i] holds instance i's state after every run()."""
 
     def __init__(self, cfgs, q_a, q_b, qt, dts, steps_per_graph: int = 10, stream=None):
@@ -509,14 +509,15 @@ class Ensemble:
             pass
 
 
-def ensemble_instances(draws=None, device="cuda"):
+def ensemble_instances(draws=None, device="cuda", mode: str = "fp32", encoding: str = "plain"):
     """The 48-instance ensemble workload: (cfgs, dts) from tgv_inputs'
-    seeded draws, dt_i = min(0.004, 0.8 dt_max,i)."""
+    seeded draws, dt_i = min(0.004, 0.8 dt_max,i); FP32 by default, any
+    precision mode on request."""
     import tgv_inputs
     draws = draws if draws is not None else tgv_inputs.ensemble_draws()
     cfgs, dts = [], []
     for n, re, m in draws:
-        c = Config(n=n, mode="fp32", re=re, mach=m)
+        c = Config(n=n, mode=mode, re=re, mach=m, encoding=encoding)
         cfgs.append(c)
         dts.append(min(0.004, 0.8 * tgv_dt_max(c)))
     return cfgs, dts

@@ -9,6 +9,7 @@
 #include "tgv_common.cuh"
 #include "tgv_stage.cuh"
 #include "tgv_init_diag.cuh"
+#include "tgv_ensemble.cuh"
 
 namespace tgv {
 
@@ -56,6 +57,8 @@ struct ModeLaunchers {
   OccFn occupancy[NUM_TILES];    // resident CTAs per SM of the EPI_RK kernel
   size_t smem[NUM_TILES];        // dynamic shared memory per CTA
   int first_tile = 0;            // tile tried before the table order
+  EnsFn ens[NUM_TILES];          // batched-ensemble stage (quadratic splits)
+  OccFn ens_occ[NUM_TILES];      // its resident CTAs per SM
   InitFn init;
   DiagFn diag_partial;
 };
@@ -130,6 +133,8 @@ void set_tile(ModeLaunchers& L, int t) {
   }
   L.occupancy[t] = stage_occupancy<TS, TT, TC, TA, TX, TY, NP>;
   L.smem[t] = stage_smem_bytes<TS, TT, TC, TX, TY, NP>();
+  L.ens[t] = ens_launch<TS, TT, TC, TA, TX, TY, NP>;
+  L.ens_occ[t] = ens_occupancy<TS, TT, TC, TA, TX, TY, NP>;
 }
 
 // WITH_KGP: also build the KGP, KEEP and Feiereisen splits (the FP64, FP32

@@ -96,3 +96,30 @@ def test_ensemble_instance_matches_oracle_in_fp32_tolerance():
     mom = float(torch.linalg.vector_norm(got[1:4] - ref[1:4]) / torch.linalg.vector_norm(ref[1:4]))
     assert mom < 1e-5 and err[0] < 1e-6 and err[4] < 1e-6, (mom, err)
     ens.close()
+
+
+@pytest.mark.parametrize("mode,enc", [("hpsp", "plain"), ("fp16_fp32", "offset"),
+                                      ("fp16", "offset"), ("spdp", "plain"), ("fp64", "plain")])
+def test_ensemble_in_every_precision_mode_matches_solo_runs(mode, enc):
+    """The ensemble in the other precision modes (one mode per ensemble): each
+    instance equals the single-instance rk_step with the ensemble's tile and
+    z chunk, bit for bit."""
+    cfgs = [tgv.Config(n=n, mode=mode, re=re, mach=m, encoding=enc)
+            for n, re, m in ((32, 400.0, 0.1), (48, 800.0, 0.2), (40, 1600.0, 0.1))]
+    dts = [min(0.004, 0.8 * tgv.tgv_dt_max(c)) for c in cfgs]
+    qa, qb, qt = _alloc(cfgs)
+    ens = tgv.Ensemble(cfgs, qa, qb, qt, dts, steps_per_graph=2)
+    info = ens.info()
+    ens.run(2)
+    torch.cuda.synchronize()
+    for i, c in enumerate(cfgs):
+        assert torch.equal(qa[i], _solo(c, dts[i], 4, info["tile"], info["zchunk_target"])), i
+    ens.close()
+
+
+def test_ensemble_refuses_mixed_precision_modes():
+    cfgs = [tgv.Config(n=32, mode="fp32"), tgv.Config(n=32, mode="hpsp")]
+    qa, qb, qt = _alloc(cfgs)
+    with pytest.raises(tgv.TGVError) as ei:
+        tgv.Ensemble(cfgs, qa, qb, qt, [0.004, 0.004])
+    assert ei.value.status == tgv._abi.TGV_ERR_ARG
