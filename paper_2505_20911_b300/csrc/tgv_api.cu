@@ -272,7 +272,13 @@ static int32_t launch_stage_common(const tgv_config* cfg, const StageArgs& S, bo
                 : cfg->split_form == TGV_SPLIT_KEEP     ? SPL_KEEP
                 : cfg->split_form == TGV_SPLIT_FEIEREISEN ? SPL_FEIER
                                                          : SPL_QUAD;
-  const StageFn fn = rhs ? L.rhs[v][tile] : (S.diag_part ? L.stage_diag[v][tile] : L.stage[v][tile]);
+  StageFn fn = rhs ? L.rhs[v][tile] : (S.diag_part ? L.stage_diag[v][tile] : L.stage[v][tile]);
+  // rk_step's stages (increment kept divided by dt, written by all but the
+  // last, read by all but the first) have kernels with those flags built in
+  if (!rhs && !S.diag_part && v == SPL_QUAD && S.scaled_qt && (S.read_qt || S.write_qt)) {
+    const int i = !S.read_qt ? 0 : (S.write_qt ? 1 : 2);
+    fn = L.stage_rk[i][tile];
+  }
   if (!fn) return TGV_ERR_UNSUPPORTED;
   cudaError_t e = fn(P, A, zc, st);
   return e == cudaSuccess ? TGV_OK : TGV_ERR_CUDA;

@@ -52,6 +52,7 @@ using DiagFn = cudaError_t (*)(const Problem&, const void*, double*, int, cudaSt
 constexpr int NUM_SPL = 4;
 struct ModeLaunchers {
   StageFn stage[NUM_SPL][NUM_TILES];      // EPI_RK (null where a mode does not build it)
+  StageFn stage_rk[3][NUM_TILES];         // EPI_RK, quadratic split, flags RKF_STAGE(i)
   StageFn stage_diag[NUM_SPL][NUM_TILES]; // EPI_RK with the fused diagnostics of its input
   StageFn rhs[NUM_SPL][NUM_TILES];        // EPI_RHS
   OccFn occupancy[NUM_TILES];    // resident CTAs per SM of the EPI_RK kernel
@@ -69,9 +70,9 @@ const ModeLaunchers& mode_launchers(int mode);
 int find_mode(const tgv_config& c);
 
 template <class TS, class TT, class TC, class TA, int TX, int TY, int NP, int EPI, bool DIAG,
-          int SPL = SPL_QUAD>
+          int SPL = SPL_QUAD, int RKF = RKF_RUNTIME>
 cudaError_t launch_stage(const Problem& P, const StageArgs& S, int zchunk, cudaStream_t st) {
-  auto kern = stage_kernel<TS, TT, TC, TA, TX, TY, NP, EPI, DIAG, SPL>;
+  auto kern = stage_kernel<TS, TT, TC, TA, TX, TY, NP, EPI, DIAG, SPL, RKF>;
   const size_t smem = stage_smem_bytes<TS, TT, TC, TX, TY, NP>();
   if (smem > STAGE_SMEM_LIMIT) return cudaErrorInvalidConfiguration;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -82,6 +83,19 @@ cudaError_t launch_stage(const Problem& P, const StageArgs& S, int zchunk, cudaS
   dim3 block(TX / NP, TY);
   kern<<<grid, block, smem, st>>>(P, S);
   return cudaGetLastError();
+}
+
+// Stage i of rk_step (quadratic split, no diagnostics): the kernel with the
+// RK flags of that stage fixed at compile time.  Its plain-encoding flag
+// matters only to FP32 storage with FP32 arithmetic; a config with another
+// encoding there takes the runtime-flag kernel.
+template <class TS, class TT, class TC, class TA, int TX, int TY, int NP, int I>
+cudaError_t launch_stage_rk(const Problem& P, const StageArgs& S, int zchunk, cudaStream_t st) {
+  constexpr bool QIN_FC = std::is_same<TS, float>::value && std::is_same<TC, float>::value;
+  if (QIN_FC && P.encoding != TGV_ENC_PLAIN)
+    return launch_stage<TS, TT, TC, TA, TX, TY, NP, EPI_RK, false, SPL_QUAD>(P, S, zchunk, st);
+  return launch_stage<TS, TT, TC, TA, TX, TY, NP, EPI_RK, false, SPL_QUAD, RKF_STAGE(I)>(P, S, zchunk,
+                                                                                       st);
 }
 
 template <class TS, class TT, class TC, class TA, int TX, int TY, int NP>
@@ -126,6 +140,9 @@ template <class TS, class TT, class TC, class TA, int TX, int TY, int NP, bool W
 void set_tile(ModeLaunchers& L, int t) {
   for (int v = 0; v < NUM_SPL; ++v) L.stage[v][t] = L.stage_diag[v][t] = L.rhs[v][t] = nullptr;
   set_split<TS, TT, TC, TA, TX, TY, NP, SPL_QUAD>(L, t);
+  L.stage_rk[0][t] = launch_stage_rk<TS, TT, TC, TA, TX, TY, NP, 0>;
+  L.stage_rk[1][t] = launch_stage_rk<TS, TT, TC, TA, TX, TY, NP, 1>;
+  L.stage_rk[2][t] = launch_stage_rk<TS, TT, TC, TA, TX, TY, NP, 2>;
   if constexpr (WITH_KGP) {
     set_split<TS, TT, TC, TA, TX, TY, NP, SPL_KGP>(L, t);
     set_split<TS, TT, TC, TA, TX, TY, NP, SPL_KEEP>(L, t);

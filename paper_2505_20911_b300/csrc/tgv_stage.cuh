@@ -56,6 +56,14 @@ enum { EPI_RK = 0, EPI_RHS = 1 };
 // The Feiereisen quadratic split (printed in Sec. 2.3.1) is the fourth:
 // 1/2 D_j(rho u_j phi) + 1/2 (phi D_j(rho u_j) + rho u_j D_j phi).
 enum { SPL_QUAD = 0, SPL_KGP = 1, SPL_KEEP = 2, SPL_FEIER = 3 };
+// RK epilogue flags fixed at compile time (kernel template argument RKF):
+// read the increment, write it, keep it divided by dt, and (FP32 storage and
+// arithmetic) plain encoding.  RKF_RUNTIME takes them from StageArgs/Problem.
+// rk_step's three stages are the combinations RKF_STAGE(i).
+enum { RKF_RUNTIME = -1, RKF_READ = 1, RKF_WRITE = 2, RKF_SCALED = 4, RKF_PLAIN = 8 };
+__host__ __device__ constexpr int RKF_STAGE(int i) {
+  return (i != 0 ? RKF_READ : 0) | (i != 2 ? RKF_WRITE : 0) | RKF_SCALED | RKF_PLAIN;
+}
 
 struct StageArgs {
   const void* q_in;   // Q layout, storage type TS
@@ -232,7 +240,7 @@ __device__ __forceinline__ void keep_extra(const int j, const Taps<V>& U, const 
 }
 
 template <class TS, class TT, class TC, class TA, int TX, int TY, int NP, int EPI, bool DIAG,
-          int SPL = SPL_QUAD>
+          int SPL = SPL_QUAD, int RKF = RKF_RUNTIME>
 __device__ __forceinline__ void stage_tile(const Problem& P, const StageArgs& S, const int x0,
                                            const int y0, const int z0, const long long cta) {
   using G = Geo<TX, TY, NP>;
@@ -248,6 +256,7 @@ __device__ __forceinline__ void stage_tile(const Problem& P, const StageArgs& S,
   const int n = P.n;
   const long long nn = (long long)n * n, n3 = nn * n;
   const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * TXU + tx;
+  __builtin_assume(tx < TXU && ty < TY);  // the launch's block shape
   const int zg = S.zg, nzl = S.nzl > 0 ? S.nzl : n;
   const long long fsq = S.fs_q > 0 ? S.fs_q : n3, fst = S.fs_t > 0 ? S.fs_t : n3;
   const int z1 = min(z0 + S.zchunk, nzl);
@@ -284,12 +293,15 @@ __device__ __forceinline__ void stage_tile(const Problem& P, const StageArgs& S,
   const int zbase = z0 - 2;
   // staging slot of raw plane zl (RS is a power of two)
   auto raw_plane = [&](int zl) -> RawS* { return stage_q + ((zl - zbase) & (RS - 1)) * 5 * PLU; };
-  int goff[PERU], eoff[PERU], tform[PERU];  // tform: 1 swap lanes, 2 -rho u, 4 -rho v
+  // Global addresses are formed as a CTA-uniform 64-bit base (plane,
+  // component) plus a 32-bit per-thread offset within the plane (n <= 1024).
+  unsigned goff[PERU];
+  int eoff[PERU], tform[PERU];  // tform: 1 swap lanes, 2 -rho u, 4 -rho v
   const bool sym = P.symmetric != 0;
 #pragma unroll
   for (int r = 0; r < PERU; ++r) {
     const int q = tid + r * NT;
-    goff[r] = -1;
+    goff[r] = 0;
     eoff[r] = 0;
     tform[r] = 0;
     if (q < PLU) {
@@ -318,25 +330,25 @@ __device__ __forceinline__ void stage_tile(const Problem& P, const StageArgs& S,
       gx = wrap_index(gx + (sym ? NP - 1 : 0), n, sym, &fx);
       if (!fx && sym) gx -= NP - 1;
       gy = wrap_index(gy, n, sym, &fy);
-      goff[r] = gy * n + gx;
+      goff[r] = (unsigned)(gy * n + gx);
       eoff[r] = ry * RX + rx;
       tform[r] = (fx && NP == 2 ? 1 : 0) | (fx ? 2 : 0) | (fy ? 4 : 0);
     }
   }
-  const long long tile_off = (long long)(y0 + ty) * n + (x0 + NP * tx);
+  const unsigned tile_off = (unsigned)((y0 + ty) * n + (x0 + NP * tx));
   const bool active_xy = (x0 + NP * tx < n) && (y0 + ty < n);
   auto prefetch = [&](int zl) {  // cp.async of raw plane zl into its staging slot
     bool fz;
     const int zw = zg ? zl + zg : wrap_near(zl, n, sym, &fz);
-    const long long zoff = (long long)zw * nn;
+    const TS* plane = q_in + (long long)zw * nn;
     RawS* dst = raw_plane(zl);
 #pragma unroll
     for (int r = 0; r < PERU; ++r) {
-      if (goff[r] >= 0) {
-        const int q = tid + r * NT;
+      const int q = tid + r * NT;
+      if (q < PLU) {
 #pragma unroll
         for (int c = 0; c < 5; ++c)
-          cp_async<sizeof(RawS)>(dst + c * PLU + q, q_in + zoff + goff[r] + c * fsq);
+          cp_async<sizeof(RawS)>(dst + c * PLU + q, plane + c * fsq + goff[r]);
       }
     }
   };
@@ -346,7 +358,7 @@ __device__ __forceinline__ void stage_tile(const Problem& P, const StageArgs& S,
     RawT* dst = stage_t;
 #pragma unroll
     for (int c = 0; c < 5; ++c)
-      cp_async<sizeof(RawT)>(dst + c * NT + tid, qt + (long long)kq * nn + tile_off + c * fst);
+      cp_async<sizeof(RawT)>(dst + c * NT + tid, qt + (long long)kq * nn + c * fst + tile_off);
   };
   // The epilogue's Q_in of the own unit, in storage precision:
   //  - four raw planes staged (raw_slots): read from the staging of its plane;
@@ -358,7 +370,11 @@ __device__ __forceinline__ void stage_tile(const Problem& P, const StageArgs& S,
   //  - otherwise: re-read from global memory at the start of phase B (a cache
   //    hit: the loader read it two planes earlier).
   constexpr bool QIN_FC = std::is_same<TS, float>::value && std::is_same<TC, float>::value;
-  const bool qin_fc = QIN_FC && P.encoding == TGV_ENC_PLAIN;
+  constexpr bool RK_CT = RKF != RKF_RUNTIME;
+  const bool read_qt = RK_CT ? (RKF & RKF_READ) != 0 : S.read_qt != 0;
+  const bool write_qt = RK_CT ? (RKF & RKF_WRITE) != 0 : S.write_qt != 0;
+  const bool scaled_qt = RK_CT ? (RKF & RKF_SCALED) != 0 : S.scaled_qt != 0;
+  const bool qin_fc = QIN_FC && (RK_CT ? (RKF & RKF_PLAIN) != 0 : P.encoding == TGV_ENC_PLAIN);
   RawS qin_raw[5];
   RawS qw_q[QIN_FC ? 3 : 1];
 #pragma unroll
@@ -468,10 +484,32 @@ __device__ __forceinline__ void stage_tile(const Problem& P, const StageArgs& S,
     }
   }
 
+  // s_z = D_x u + D_y v of the own unit at plane pl, pushed onto its queue
+  auto push_sz = [&](const TC* pl) {
+    V cdummy;
+    const V dxu = dsum(xt(pl + F_U * PL, ec, cdummy), c_8);
+    const V dyv = dsum(yt(pl + F_V * PL, ec), c_8);
+#pragma unroll
+    for (int d = 0; d < 4; ++d) szq[d] = szq[d + 1];
+    szq[4] = c_inv12h * (dxu + dyv);
+  };
+
   prefetch(zbase);
   cp_async_commit();
-  int slot = 0;  // ring slot of plane zl: (zl - zbase) mod NSLOT
-  for (int zl = zbase; zl < z1 + 2; ++zl, slot = (slot + 1 == NSLOT ? 0 : slot + 1)) {
+  // Prologue: planes z0-2 .. z0+1 are no centre plane yet; they only fill the
+  // ring and the s_z queue.  Each goes to a fresh ring slot and every thread
+  // reads back only the staging units it copied itself, so one barrier per
+  // plane suffices.
+  for (int zl = zbase; zl < z0 + 2; ++zl) {
+    cp_async_wait<0>();
+    commit(zl - zbase, zl);
+    __syncthreads();
+    prefetch(zl + 1);  // z0 + 2 < z1 + 2: the main loop below consumes it
+    cp_async_commit();
+    push_sz(ring + (zl - zbase) * NFLD * PL);
+  }
+  int slot = 4;  // ring slot of plane zl: (zl - zbase) mod NSLOT
+  for (int zl = z0 + 2; zl < z1 + 2; ++zl, slot = (slot + 1 == NSLOT ? 0 : slot + 1)) {
     cp_async_wait<0>();
     commit(slot, zl);
     __syncthreads();
@@ -479,14 +517,14 @@ __device__ __forceinline__ void stage_tile(const Problem& P, const StageArgs& S,
     // then the next raw plane (a second group, waited for by the next
     // iteration); one Qt staging plane suffices because every thread reads
     // only the unit it copied, in the epilogue of this same iteration
-    if (EPI == EPI_RK && S.read_qt && zl - 2 >= z0 && zl - 2 < z1) {
+    if (EPI == EPI_RK && read_qt) {
       prefetch_qt(zl - 2);
       cp_async_commit();
     }
     if (zl + 1 < z1 + 2) prefetch(zl + 1);
     cp_async_commit();
 
-    const int k = zl - 2;
+    const int k = zl - 2;  // centre plane, z0 <= k < z1
     const TC* pk[5];  // ring planes k-2 .. k+2 = zl-4 .. zl: slots slot+1 .. slot+5 (mod NSLOT)
 #pragma unroll
     for (int d = 0; d < 5; ++d) {
@@ -496,22 +534,14 @@ __device__ __forceinline__ void stage_tile(const Problem& P, const StageArgs& S,
     TC* st = strips;
 
     // ---- phase A: s_z of plane zl (own unit, kept in registers) ...
-    {
-      const TC* pl = ring + slot * NFLD * PL;
-      V cdummy;
-      const V dxu = dsum(xt(pl + F_U * PL, ec, cdummy), c_8);
-      const V dyv = dsum(yt(pl + F_V * PL, ec), c_8);
-#pragma unroll
-      for (int d = 0; d < 4; ++d) szq[d] = szq[d + 1];
-      szq[4] = c_inv12h * (dxu + dyv);
-    }
+    push_sz(ring + slot * NFLD * PL);
     // ... then, for centre plane k: the strip fields of the tile and its halo,
     // and every z-direction term of the own unit (its z taps of u, v, w are
     // shared with the strips).  The partial sums stay in registers across the
     // barrier and phase B adds the x and y directions.
     // Per-unit values of the centre plane.  Phase A assigns each of them (the
     // z-direction terms are the first contribution to every sum, so no sum
-    // starts from a zero fill); phase B runs only where phase A did.
+    // starts from a zero fill).
     V fc[5], uc[3], h0c, div;
     V fcc[5];  // rho phi of the convective split (KEEP: rho e in place of rho E)
     V pc;      // centre pressure (KEEP)
@@ -523,7 +553,7 @@ __device__ __forceinline__ void stage_tile(const Problem& P, const StageArgs& S,
 #pragma unroll
       for (int c = 0; c < 5; ++c) kx[c] = zero;
     }
-    if (k >= z0) {
+    {
       const TC* P0 = pk[2];
       auto ztw = [&](int fld, int e) -> Taps<V> {
         return {V::load(pk[0] + fld * PL + e), V::load(pk[1] + fld * PL + e),
@@ -638,7 +668,7 @@ __device__ __forceinline__ void stage_tile(const Problem& P, const StageArgs& S,
     __syncthreads();
 
     // ---- phase B: x- and y-direction terms of the own unit, assembly, epilogue
-    if (k >= z0 && active_xy) {
+    if (active_xy) {
       const TC* P0 = pk[2];
       // the epilogue's Q_in of the own unit at plane k (see qin_raw), issued
       // here so that its latency hides behind the x/y terms
@@ -651,7 +681,7 @@ __device__ __forceinline__ void stage_tile(const Problem& P, const StageArgs& S,
           if (!qin_fc) {
 #pragma unroll
             for (int c = 0; c < 5; ++c)
-              qin_raw[c] = IO::load(q_in + (long long)(k + zg) * nn + tile_off + c * fsq);
+              qin_raw[c] = IO::load(q_in + (long long)(k + zg) * nn + c * fsq + tile_off);
           }
         }
       }
@@ -763,21 +793,27 @@ __device__ __forceinline__ void stage_tile(const Problem& P, const StageArgs& S,
         dacc[9].add((typename DA::In)bad);
       }
 
-      const long long o = (long long)k * nn + tile_off;
+      const long long ko = (long long)k * nn;  // centre plane (plus tile_off per thread)
       if constexpr (EPI == EPI_RHS) {
         TC* r_out = static_cast<TC*>(S.r_out);
 #pragma unroll
-        for (int c = 0; c < 5; ++c) R[c].store(r_out + o + c * fst);
+        for (int c = 0; c < 5; ++c) R[c].store(r_out + ko + c * fst + tile_off);
       } else {
         TS* q_out = static_cast<TS*>(S.q_out);
         TT* qt = static_cast<TT*>(S.qt);
         const TA a = cvt<TA>(S.a), b = cvt<TA>(S.b), dt = cvt<TA>(S.dt);
         const TA bdt = cvt<TA>(S.bdt);
-        if (S.read_qt) cp_async_wait<1>();  // all but the newest group (the next raw plane)
+        if (read_qt) cp_async_wait<1>();  // all but the newest group (the next raw plane)
         const RawT* qts = stage_t;
+        // With FP32 accumulation on two lanes the update runs as paired
+        // instructions (f32x2): per lane the same fused multiply-adds, with the
+        // same rounding, as the scalar form, which every other kernel that
+        // inlines this epilogue (the ensemble's) shares.
+        constexpr bool PAIRED = std::is_same<TA, float>::value && NP == 2;
+        using VA = Vec<TA, NP>;
 #pragma unroll
         for (int c = 0; c < 5; ++c) {
-          TA qtn[NP], qo[NP], qin[NP], qold[NP];
+          TA qtn[NP], qo[NP], qin[NP], qold[NP], rc[NP];
           if constexpr (QIN_FC) {
             if (qin_fc) {
               if (c == 3) raw_elems<TA, NP>(qw_q[2], qin);
@@ -791,25 +827,29 @@ __device__ __forceinline__ void stage_tile(const Problem& P, const StageArgs& S,
           } else {
             raw_elems<TA, NP>(qin_raw[c], qin);
           }
-          if (S.read_qt) raw_elems<TA, NP>(qts[c * NT + tid], qold);
+          if (read_qt) raw_elems<TA, NP>(qts[c * NT + tid], qold);
 #pragma unroll
-          for (int e = 0; e < NP; ++e) {
-            // explicit fused multiply-adds: the same rounding in every kernel
-            // that inlines this epilogue (rk_step's and the ensemble's)
-            if (S.scaled_qt) {
-              TA v = cvt<TA>(R[c].get(e));
-              if (S.read_qt) v = fma_rn(a, qold[e], v);
+          for (int e = 0; e < NP; ++e) rc[e] = cvt<TA>(R[c].get(e));
+          if constexpr (PAIRED) {
+            VA v = scaled_qt ? VA(rc[0], rc[1]) : VA::splat(dt) * VA(rc[0], rc[1]);
+            if (read_qt) v = fma(VA::splat(a), VA(qold[0], qold[1]), v);
+            const VA w = fma(VA::splat(scaled_qt ? bdt : b), v, VA(qin[0], qin[1]));
+            qtn[0] = v.get(0);
+            qtn[1] = v.get(1);
+            qo[0] = w.get(0);
+            qo[1] = w.get(1);
+          } else {
+#pragma unroll
+            for (int e = 0; e < NP; ++e) {
+              // explicit fused multiply-adds (the rounding of the paired form)
+              TA v = scaled_qt ? rc[e] : dt * rc[e];
+              if (read_qt) v = fma_rn(a, qold[e], v);
               qtn[e] = v;
-              qo[e] = fma_rn(bdt, v, qin[e]);
-            } else {
-              TA v = dt * cvt<TA>(R[c].get(e));
-              if (S.read_qt) v = fma_rn(a, qold[e], v);
-              qtn[e] = v;
-              qo[e] = fma_rn(b, v, qin[e]);
+              qo[e] = fma_rn(scaled_qt ? bdt : b, v, qin[e]);
             }
           }
-          UnitStore<TS, NP>::put(q_out + o + zg * nn + c * fsq, qo);
-          if (S.write_qt) UnitStore<TT, NP>::put(qt + o + c * fst, qtn);
+          UnitStore<TS, NP>::put(q_out + ko + zg * nn + c * fsq + tile_off, qo);
+          if (write_qt) UnitStore<TT, NP>::put(qt + ko + c * fst + tile_off, qtn);
         }
       }
     }
@@ -842,12 +882,12 @@ template <class TC> constexpr int stage_min_blocks() {
 }
 
 template <class TS, class TT, class TC, class TA, int TX, int TY, int NP, int EPI, bool DIAG,
-          int SPL = SPL_QUAD>
+          int SPL = SPL_QUAD, int RKF = RKF_RUNTIME>
 __global__ void __launch_bounds__(Geo<TX, TY, NP>::NT, stage_min_blocks<TC>())
 stage_kernel(const Problem P, const StageArgs S) {
   const long long cta = ((long long)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
-  stage_tile<TS, TT, TC, TA, TX, TY, NP, EPI, DIAG, SPL>(P, S, blockIdx.x * TX, blockIdx.y * TY,
-                                                         blockIdx.z * S.zchunk, cta);
+  stage_tile<TS, TT, TC, TA, TX, TY, NP, EPI, DIAG, SPL, RKF>(
+      P, S, blockIdx.x * TX, blockIdx.y * TY, blockIdx.z * S.zchunk, cta);
 }
 
 }  // namespace tgv
