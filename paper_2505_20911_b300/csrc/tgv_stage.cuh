@@ -60,9 +60,14 @@ enum { SPL_QUAD = 0, SPL_KGP = 1, SPL_KEEP = 2, SPL_FEIER = 3 };
 // read the increment, write it, keep it divided by dt, and (FP32 storage and
 // arithmetic) plain encoding.  RKF_RUNTIME takes them from StageArgs/Problem.
 // rk_step's three stages are the combinations RKF_STAGE(i).
-enum { RKF_RUNTIME = -1, RKF_READ = 1, RKF_WRITE = 2, RKF_SCALED = 4, RKF_PLAIN = 8 };
+// RKF_ENC_RT keeps only the encoding a run-time choice (the ensemble, whose
+// instances may differ in it).
+enum { RKF_RUNTIME = -1, RKF_READ = 1, RKF_WRITE = 2, RKF_SCALED = 4, RKF_PLAIN = 8, RKF_ENC_RT = 16 };
 __host__ __device__ constexpr int RKF_STAGE(int i) {
   return (i != 0 ? RKF_READ : 0) | (i != 2 ? RKF_WRITE : 0) | RKF_SCALED | RKF_PLAIN;
+}
+__host__ __device__ constexpr int RKF_STAGE_ENC_RT(int i) {
+  return (i != 0 ? RKF_READ : 0) | (i != 2 ? RKF_WRITE : 0) | RKF_SCALED | RKF_ENC_RT;
 }
 
 struct StageArgs {
@@ -374,7 +379,8 @@ __device__ __forceinline__ void stage_tile(const Problem& P, const StageArgs& S,
   const bool read_qt = RK_CT ? (RKF & RKF_READ) != 0 : S.read_qt != 0;
   const bool write_qt = RK_CT ? (RKF & RKF_WRITE) != 0 : S.write_qt != 0;
   const bool scaled_qt = RK_CT ? (RKF & RKF_SCALED) != 0 : S.scaled_qt != 0;
-  const bool qin_fc = QIN_FC && (RK_CT ? (RKF & RKF_PLAIN) != 0 : P.encoding == TGV_ENC_PLAIN);
+  const bool qin_fc = QIN_FC && (RK_CT && !(RKF & RKF_ENC_RT) ? (RKF & RKF_PLAIN) != 0
+                                                              : P.encoding == TGV_ENC_PLAIN);
   RawS qin_raw[5];
   RawS qw_q[QIN_FC ? 3 : 1];
 #pragma unroll
@@ -384,13 +390,22 @@ __device__ __forceinline__ void stage_tile(const Problem& P, const StageArgs& S,
     bool fz;
     wrap_near(zl, n, sym, &fz);
     const RawS* src = raw_plane(zl);
+    // every unit's staged values are read before the first ring store (a
+    // store may alias the staging for the compiler and hold later loads back)
+    RawS raws[PERU][5];
 #pragma unroll
     for (int r = 0; r < PERU; ++r) {
       const int q = tid + r * NT;
       if (q < PLU) {
-        RawS raw[5];
 #pragma unroll
-        for (int c = 0; c < 5; ++c) raw[c] = src[c * PLU + q];
+        for (int c = 0; c < 5; ++c) raws[r][c] = src[c * PLU + q];
+      }
+    }
+#pragma unroll
+    for (int r = 0; r < PERU; ++r) {
+      const int q = tid + r * NT;
+      if (q < PLU) {
+        const RawS* raw = raws[r];
         if constexpr (QIN_FC) {
           if (r == 0) {
             qw_q[2] = qw_q[1];
@@ -559,7 +574,10 @@ __device__ __forceinline__ void stage_tile(const Problem& P, const StageArgs& S,
         return {V::load(pk[0] + fld * PL + e), V::load(pk[1] + fld * PL + e),
                 V::load(pk[3] + fld * PL + e), V::load(pk[4] + fld * PL + e)};
       };
-      // own unit (tile point)
+      // own unit (tile point); its strip values are stored at the end of the
+      // phase, after every ring load of the phase (a shared store may alias
+      // the ring for the compiler, which then keeps later loads behind it)
+      V own_sx, own_sy, own_gx, own_gy;
       {
         h0c = V::load(P0 + F_H0 * PL + ec);
         const Taps<V> ux = xt(P0 + F_U * PL, ec, uc[0]);
@@ -584,13 +602,13 @@ __device__ __forceinline__ void stage_tile(const Problem& P, const StageArgs& S,
         const V dyv = c_inv12h * dsum(vy, c_8);
         const V dzw = c_inv12h * dsum(wz, c_8);
         div = dxu + dyv + dzw;
-        (dyv + dzw).store(st + S_SX * PL + ec);
-        (dxu + dzw).store(st + S_SY * PL + ec);
+        own_sx = dyv + dzw;
+        own_sy = dxu + dzw;
         const V eyuv = dsum(tmul(uy, vy), c_8);
         const V ezuw = dsum(tmul(uz, wz), c_8);
         const V ezvw = dsum(tmul(vz, wz), c_8);
-        (c_2 * c_inv12h * (eyuv + ezuw)).store(st + S_GX * PL + ec);
-        (c_2 * c_inv12h * ezvw).store(st + S_GY * PL + ec);
+        own_gx = c_2 * c_inv12h * (eyuv + ezuw);
+        own_gy = c_2 * c_inv12h * ezvw;
 
         // z-direction terms (j = 2)
         const Taps<V>& U = wz;
@@ -648,22 +666,27 @@ __device__ __forceinline__ void stage_tile(const Problem& P, const StageArgs& S,
       for (int r = 0; r < G::PERH; ++r) {
         const int e = strip_e[r];
         if (strip_kind[r] == 1) {
-          const V dyv = c_inv12h * dsum(yt(P0 + F_V * PL, e), c_8);
-          const Taps<V> wz = ztw(F_W, e);
+          const Taps<V> vy = yt(P0 + F_V * PL, e), wz = ztw(F_W, e);
+          const V dyv = c_inv12h * dsum(vy, c_8);
           const V dzw = c_inv12h * dsum(wz, c_8);
-          (dyv + dzw).store(st + S_SX * PL + e);
-          const V eyuv = dsum(tmul(yt(P0 + F_U * PL, e), yt(P0 + F_V * PL, e)), c_8);
+          const V eyuv = dsum(tmul(yt(P0 + F_U * PL, e), vy), c_8);
           const V ezuw = dsum(tmul(ztw(F_U, e), wz), c_8);
+          (dyv + dzw).store(st + S_SX * PL + e);
           (c_2 * c_inv12h * (eyuv + ezuw)).store(st + S_GX * PL + e);
         } else if (strip_kind[r] == 2) {
           V cd;
           const V dxu = c_inv12h * dsum(xt(P0 + F_U * PL, e, cd), c_8);
           const Taps<V> wz = ztw(F_W, e);
           const V dzw = c_inv12h * dsum(wz, c_8);
+          const V ezvw = dsum(tmul(ztw(F_V, e), wz), c_8);
           (dxu + dzw).store(st + S_SY * PL + e);
-          (c_2 * c_inv12h * dsum(tmul(ztw(F_V, e), wz), c_8)).store(st + S_GY * PL + e);
+          (c_2 * c_inv12h * ezvw).store(st + S_GY * PL + e);
         }
       }
+      own_sx.store(st + S_SX * PL + ec);
+      own_sy.store(st + S_SY * PL + ec);
+      own_gx.store(st + S_GX * PL + ec);
+      own_gy.store(st + S_GY * PL + ec);
     }
     __syncthreads();
 

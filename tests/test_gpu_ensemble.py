@@ -99,11 +99,15 @@ def test_ensemble_instance_matches_oracle_in_fp32_tolerance():
 
 
 @pytest.mark.parametrize("mode,enc", [("hpsp", "plain"), ("fp16_fp32", "offset"),
-                                      ("fp16", "offset"), ("spdp", "plain"), ("fp64", "plain")])
+                                      ("fp16", "offset"), ("spdp", "plain"), ("fp64", "plain"),
+                                      ("hpsp", "offset"), ("fp32", "offset")])
 def test_ensemble_in_every_precision_mode_matches_solo_runs(mode, enc):
     """The ensemble in the other precision modes (one mode per ensemble): each
     instance equals the single-instance rk_step with the ensemble's tile and
-    z chunk, bit for bit."""
+    z chunk, bit for bit.  The ensemble's kernel reads the RK flags at run
+    time, rk_step's stages have them built in; FP32 storage with FP32
+    arithmetic and the offset encoding takes rk_step's runtime-flag kernel
+    (its built-in flags assume the plain encoding)."""
     cfgs = [tgv.Config(n=n, mode=mode, re=re, mach=m, encoding=enc)
             for n, re, m in ((32, 400.0, 0.1), (48, 800.0, 0.2), (40, 1600.0, 0.1))]
     dts = [min(0.004, 0.8 * tgv.tgv_dt_max(c)) for c in cfgs]
