@@ -34,7 +34,7 @@ struct EnsTable {
 // the encoding read per instance), so an instance matches a single-instance
 // rk_step with the same tile and z chunk bit for bit.
 template <class TS, class TT, class TC, class TA, int TX, int TY, int NP, int I>
-__global__ void __launch_bounds__(Geo<TX, TY, NP>::NT, stage_min_blocks<TC>())
+__global__ void __launch_bounds__(Geo<TX, TY, NP>::NT, stage_min_blocks<TC, TX, TY, NP>())
 ensemble_stage_kernel(const EnsTable T, const double a, const double b, const int parity) {
   for (int item = blockIdx.x; item < T.total_items; item += gridDim.x) {
     int ii = 0;

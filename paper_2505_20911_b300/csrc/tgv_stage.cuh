@@ -93,11 +93,13 @@ struct StageArgs {
   long long fs_q, fs_t;
 };
 
-// Ring-plane fields (compute type).  rho w is not kept: its taps are formed
-// as rho * w (one multiply per tap instead of one shared-memory load).
-enum { F_RHO = 0, F_RU, F_RV, F_RE, F_U, F_V, F_W, F_P, F_H0, NFLD };
-// Ring field of conserved component c (rho w: none).
-__host__ __device__ constexpr int cons_field(int c) { return c < 3 ? c : (c == 4 ? F_RE : -1); }
+// Ring-plane fields (compute type).  The momenta are not kept: the taps of
+// rho u, rho v and rho w are formed as rho * u, rho * v and rho * w (one
+// multiply per tap instead of one shared-memory load; the stage is bound by
+// shared-memory bandwidth, not by FP32 issue).
+enum { F_RHO = 0, F_RE, F_U, F_V, F_W, F_P, F_H0, NFLD };
+// Ring field of conserved component c (the momenta: none).
+__host__ __device__ constexpr int cons_field(int c) { return c == 0 ? F_RHO : (c == 4 ? F_RE : -1); }
 // Strip fields of the centre plane.
 enum { S_SX = 0, S_SY, S_GX, S_GY, NSTRIP };
 // Ring depth: phase A of centre plane k reads planes k-2..k+2; phase B reads
@@ -253,10 +255,11 @@ __device__ __forceinline__ void stage_tile(const Problem& P, const StageArgs& S,
   using IO = UnitIO<TC, NP, TS>;
   constexpr int RX = G::RX, PL = G::PL, NT = G::NT, RXU = G::RXU, PLU = G::PLU;
   constexpr int PERU = G::PERU, TXU = G::TXU;
+  constexpr int NF = NFLD;
 
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  TC* ring = reinterpret_cast<TC*>(smem_raw);         // [NSLOT][NFLD][PL]
-  TC* strips = ring + NSLOT * NFLD * PL;               // [NSTRIP][PL]
+  TC* ring = reinterpret_cast<TC*>(smem_raw);         // [NSLOT][NF][PL]
+  TC* strips = ring + NSLOT * NF * PL;                 // [NSTRIP][PL]
 
   const int n = P.n;
   const long long nn = (long long)n * n, n3 = nn * n;
@@ -367,14 +370,32 @@ __device__ __forceinline__ void stage_tile(const Problem& P, const StageArgs& S,
   };
   // The epilogue's Q_in of the own unit, in storage precision:
   //  - four raw planes staged (raw_slots): read from the staging of its plane;
-  //  - FP32 storage and arithmetic, plain encoding: rho, rho u, rho v and
-  //    rho E of the centre plane are already in registers as exact copies of
-  //    the stored values (fc below); rho w, which the ring does not hold, is
+  //  - FP32 storage and arithmetic, plain encoding: rho and rho E of the
+  //    centre plane are already in registers as exact copies of the stored
+  //    values (fc below); the momenta, which the ring does not hold, are
   //    carried from the plane loader in a three-plane register queue (planes
   //    zl, zl-1, zl-2; zeroed first, so no entry is read before it is written);
   //  - otherwise: re-read from global memory at the start of phase B (a cache
   //    hit: the loader read it two planes earlier).
   constexpr bool QIN_FC = std::is_same<TS, float>::value && std::is_same<TC, float>::value;
+  // Own-unit z taps from registers (FP32 arithmetic, quadratic splits): the
+  // loader keeps the primitives of its own unit for the last five planes
+  // (zq[s][field] holds the plane committed to ring slot s), so the
+  // z-direction terms read no shared memory; the ring still serves the x and
+  // y taps and the z taps of the halo strips.  The z march is unrolled by the
+  // ring depth, so every slot index is a compile-time constant and the
+  // register queues are never shifted.  Only the 32x16 tile: the smaller
+  // tiles hold two region units per thread and would spill (their FP32
+  // kernel serves the FP64-state mode, two CTAs per SM).  Not in the
+  // fused-diagnostics stage and the ensemble's persistent kernel, whose extra
+  // live values would then spill.  Either path computes the same values.
+  constexpr bool ZQ = std::is_same<TC, float>::value && NP == 2 && NT >= 256 && SPL == SPL_QUAD &&
+                      !DIAG && !(RKF != RKF_RUNTIME && (RKF & RKF_ENC_RT));
+  V zq[ZQ ? NSLOT : 1][NF];
+#pragma unroll
+  for (int d = 0; d < (ZQ ? 5 : 1); ++d)
+#pragma unroll
+    for (int f = 0; f < NF; ++f) zq[d][f] = V::splat(cvt<TC>(0.0));
   constexpr bool RK_CT = RKF != RKF_RUNTIME;
   const bool read_qt = RK_CT ? (RKF & RKF_READ) != 0 : S.read_qt != 0;
   const bool write_qt = RK_CT ? (RKF & RKF_WRITE) != 0 : S.write_qt != 0;
@@ -382,11 +403,16 @@ __device__ __forceinline__ void stage_tile(const Problem& P, const StageArgs& S,
   const bool qin_fc = QIN_FC && (RK_CT && !(RKF & RKF_ENC_RT) ? (RKF & RKF_PLAIN) != 0
                                                               : P.encoding == TGV_ENC_PLAIN);
   RawS qin_raw[5];
-  RawS qw_q[QIN_FC ? 3 : 1];
+  // raw rho u, rho v, rho w: of ring slot s (ZQ), else of planes zl, zl-1, zl-2
+  constexpr bool QM_GLOBAL = ZQ;  // momenta re-read from global memory
+  constexpr int NQM = QIN_FC && !QM_GLOBAL ? 3 : 1;
+  RawS qm_q[NQM][3];
 #pragma unroll
-  for (int d = 0; d < (QIN_FC ? 3 : 1); ++d) qw_q[d] = RawS{};
+  for (int d = 0; d < NQM; ++d)
+#pragma unroll
+    for (int m = 0; m < 3; ++m) qm_q[d][m] = RawS{};
   auto commit = [&](int slot, int zl) {  // staged raw plane -> primitives in the ring
-    TC* base = ring + slot * NFLD * PL;
+    TC* base = ring + slot * NF * PL;
     bool fz;
     wrap_near(zl, n, sym, &fz);
     const RawS* src = raw_plane(zl);
@@ -408,9 +434,14 @@ __device__ __forceinline__ void stage_tile(const Problem& P, const StageArgs& S,
         const RawS* raw = raws[r];
         if constexpr (QIN_FC) {
           if (r == 0) {
-            qw_q[2] = qw_q[1];
-            qw_q[1] = qw_q[0];
-            qw_q[0] = raw[3];
+#pragma unroll
+            for (int m = 0; m < 3; ++m) {
+              if constexpr (!QM_GLOBAL) {
+                qm_q[2][m] = qm_q[1][m];
+                qm_q[1][m] = qm_q[0][m];
+                qm_q[0][m] = raw[1 + m];
+              }
+            }
           }
         }
         const int e = eoff[r];
@@ -433,9 +464,18 @@ __device__ __forceinline__ void stage_tile(const Problem& P, const StageArgs& S,
         const V p = c_gm1 * (rE - ke);
         const V T = c_gM2 * p * ri;
         const V h0 = fma(c_kappa, T, c_nuh * fma(uu, uu, fma(vv, vv, ww * ww)));
+        if constexpr (ZQ) {
+          if (r == 0) {  // the own unit
+            zq[slot][F_RHO] = rho;
+            zq[slot][F_RE] = rE;
+            zq[slot][F_U] = uu;
+            zq[slot][F_V] = vv;
+            zq[slot][F_W] = ww;
+            zq[slot][F_P] = p;
+            zq[slot][F_H0] = h0;
+          }
+        }
         rho.store(base + F_RHO * PL + e);
-        ru.store(base + F_RU * PL + e);
-        rv.store(base + F_RV * PL + e);
         rE.store(base + F_RE * PL + e);
         uu.store(base + F_U * PL + e);
         vv.store(base + F_V * PL + e);
@@ -471,7 +511,7 @@ __device__ __forceinline__ void stage_tile(const Problem& P, const StageArgs& S,
   const int rxc = 2 + NP * tx, ryc = 2 + ty;
   const int ec = ryc * RX + rxc;        // unit centre in plane layout
   const V zero = V::splat(cvt<TC>(0.0));
-  V szq[5];  // s_z = D_x u + D_y v of the own unit at planes zl-4 .. zl
+  V szq[5];  // s_z = D_x u + D_y v of the own unit: of ring slot s (ZQ), else of planes zl-4 .. zl
 #pragma unroll
   for (int d = 0; d < 5; ++d) szq[d] = zero;
 
@@ -500,13 +540,17 @@ __device__ __forceinline__ void stage_tile(const Problem& P, const StageArgs& S,
   }
 
   // s_z = D_x u + D_y v of the own unit at plane pl, pushed onto its queue
-  auto push_sz = [&](const TC* pl) {
+  auto push_sz = [&](const TC* pl, int slot) {
     V cdummy;
     const V dxu = dsum(xt(pl + F_U * PL, ec, cdummy), c_8);
     const V dyv = dsum(yt(pl + F_V * PL, ec), c_8);
+    if constexpr (ZQ) {
+      szq[slot] = c_inv12h * (dxu + dyv);
+    } else {
 #pragma unroll
-    for (int d = 0; d < 4; ++d) szq[d] = szq[d + 1];
-    szq[4] = c_inv12h * (dxu + dyv);
+      for (int d = 0; d < 4; ++d) szq[d] = szq[d + 1];
+      szq[4] = c_inv12h * (dxu + dyv);
+    }
   };
 
   prefetch(zbase);
@@ -515,16 +559,28 @@ __device__ __forceinline__ void stage_tile(const Problem& P, const StageArgs& S,
   // ring and the s_z queue.  Each goes to a fresh ring slot and every thread
   // reads back only the staging units it copied itself, so one barrier per
   // plane suffices.
-  for (int zl = zbase; zl < z0 + 2; ++zl) {
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const int zl = zbase + i;  // ring slot i
     cp_async_wait<0>();
-    commit(zl - zbase, zl);
+    commit(i, zl);
     __syncthreads();
     prefetch(zl + 1);  // z0 + 2 < z1 + 2: the main loop below consumes it
     cp_async_commit();
-    push_sz(ring + (zl - zbase) * NFLD * PL);
+    push_sz(ring + i * NF * PL, i);
   }
-  int slot = 4;  // ring slot of plane zl: (zl - zbase) mod NSLOT
-  for (int zl = z0 + 2; zl < z1 + 2; ++zl, slot = (slot + 1 == NSLOT ? 0 : slot + 1)) {
+  // ring slot of plane zl: (zl - zbase) mod NSLOT; the first centre plane's
+  // iteration commits to slot 4
+  constexpr int UNR = ZQ ? NSLOT : 1;
+  for (int zl0 = z0 + 2; zl0 < z1 + 2; zl0 += NSLOT) {
+#pragma unroll UNR
+   for (int u = 0; u < NSLOT; ++u) {
+    const int zl = zl0 + u;
+    if (zl >= z1 + 2) break;
+    const int slot = (4 + u) % NSLOT;
+    // slots of planes k-2, k-1, k, k+1 of the centre plane k = zl - 2 (k+2: slot)
+    const int sm2 = (slot + 1) % NSLOT, sm1 = (slot + 2) % NSLOT, sc0 = (slot + 3) % NSLOT,
+              sp1 = (slot + 4) % NSLOT;
     cp_async_wait<0>();
     commit(slot, zl);
     __syncthreads();
@@ -544,12 +600,12 @@ __device__ __forceinline__ void stage_tile(const Problem& P, const StageArgs& S,
 #pragma unroll
     for (int d = 0; d < 5; ++d) {
       const int sd = slot + 1 + d;
-      pk[d] = ring + (sd >= NSLOT ? sd - NSLOT : sd) * NFLD * PL;
+      pk[d] = ring + (sd >= NSLOT ? sd - NSLOT : sd) * NF * PL;
     }
     TC* st = strips;
 
     // ---- phase A: s_z of plane zl (own unit, kept in registers) ...
-    push_sz(ring + slot * NFLD * PL);
+    push_sz(ring + slot * NF * PL, slot);
     // ... then, for centre plane k: the strip fields of the tile and its halo,
     // and every z-direction term of the own unit (its z taps of u, v, w are
     // shared with the strips).  The partial sums stay in registers across the
@@ -568,36 +624,122 @@ __device__ __forceinline__ void stage_tile(const Problem& P, const StageArgs& S,
 #pragma unroll
       for (int c = 0; c < 5; ++c) kx[c] = zero;
     }
+    const TC* P0 = pk[2];
+    auto ztw = [&](int fld, int e) -> Taps<V> {
+      return {V::load(pk[0] + fld * PL + e), V::load(pk[1] + fld * PL + e),
+              V::load(pk[3] + fld * PL + e), V::load(pk[4] + fld * PL + e)};
+    };
+    // the own unit's z taps and centre values: the register queue (ZQ) or the ring
+    auto zt = [&](int fld) -> Taps<V> {
+      if constexpr (ZQ) {
+        Taps<V> t{zq[sm2][fld], zq[sm1][fld], zq[sp1][fld], zq[slot][fld]};
+        pin(t.m2);
+        pin(t.m1);
+        pin(t.p1);
+        pin(t.p2);
+        return t;
+      } else {
+        return ztw(fld, ec);
+      }
+    };
+    auto zc = [&](int fld) -> V {
+      if constexpr (ZQ) {
+        V c = zq[sc0][fld];
+        pin(c);
+        return c;
+      } else {
+        return V::load(P0 + fld * PL + ec);
+      }
+    };
+    // centre-plane values of the own unit (ucx: u, when the ring serves it)
+    auto centre_values = [&](const V& ucx) {
+      h0c = zc(F_H0);
+      uc[0] = ZQ ? zc(F_U) : ucx;
+      uc[1] = zc(F_V);
+      uc[2] = zc(F_W);
+      fc[0] = zc(F_RHO);
+      fc[4] = zc(F_RE);
+#pragma unroll
+      for (int i = 0; i < 3; ++i) fc[1 + i] = fc[0] * uc[i];
+#pragma unroll
+      for (int c = 0; c < 5; ++c) fcc[c] = fc[c];
+      if constexpr (KEEP) {
+        pc = zc(F_P);
+        fcc[4] = c_ig1 * pc;
+      }
+    };
+    // z-direction terms (j = 2), the first contribution to every sum: in
+    // phase A when the z taps come from the ring (they fill the warps that
+    // have no halo strip), in phase B from the register queue (fewer values
+    // live across the barrier)
+    auto z_terms = [&]() {
+      const Taps<V> uz = zt(F_U), vz = zt(F_V), wz = zt(F_W);
+      const Taps<V>& U = wz;
+      const Taps<V> aU = tscale(c_alpha, U);
+      const Taps<V> Pt = zt(F_P);
+      V dFz[5];
+      Taps<V> F0z, F4z, Fmz[3];
+#pragma unroll
+      for (int c = 0; c < 5; ++c) {
+        const Taps<V> F = c == 3 ? tmul(F0z, U)
+                          : c == 1 ? tmul(F0z, uz)
+                          : c == 2 ? tmul(F0z, vz)
+                          : ((KEEP && c == 4) ? tscale(c_ig1, Pt) : zt(cons_field(c)));
+        const V dF = dsum(F, c_8);
+        dFz[c] = dF;
+        if (c == 0) F0z = F;
+        if constexpr (XTRA) {
+          if (c == 4) F4z = F;
+        }
+        if constexpr (KEEP) {
+          if (c >= 1 && c <= 3) Fmz[c - 1] = F;
+        }
+        udf[c] = uc[2] * dF;
+        if (c == 0) continue;
+        Taps<V> g;
+        if (c == 3) g = tfma(aU, F, Pt);                      // a w rho w + p
+        else if (c == 4 && !KEEP) g = tmul(U, taxpy(c_alpha, F, Pt));  // w (a rho E + p)
+        else g = tmul(aU, F);
+        suf[c] = dsum(g, c_8);
+        if (c == 3) suf[0] = c_alpha * dF;  // D_z(rho w)
+      }
+      if constexpr (XTRA) {
+        const Taps<V> UZall[3] = {uz, vz, wz};
+        kgp_extra<!FEIER>(2, U, UZall, F0z, F4z, dFz, fcc, uc, c_8, kx);
+        if constexpr (KEEP) keep_extra(2, U, UZall, Fmz, Pt, dFz, fc, uc, pc, c_8, c_4, kx);
+      }
+      const Taps<V>* UZ[3] = {&uz, &vz, &wz};
+#pragma unroll
+      for (int i = 0; i < 3; ++i) {
+        const V d2 = d2sum(*UZ[i], uc[i], c_16, c_m30);
+        d2u[i] = i == 2 ? c_43 * d2 : d2;
+        if constexpr (DIAG) grad[i][2] = dsum(*UZ[i], c_8);
+      }
+      {
+        const Taps<V> H = tfma(tscale(c_nu6, U), U, zt(F_H0));
+        const V Hc = fma(c_nu6 * uc[2], uc[2], h0c);
+        d2h = d2sum(H, Hc, c_16, c_m30);
+      }
+      {
+        const Taps<V> Sj = ZQ ? Taps<V>{szq[sm2], szq[sm1], szq[sp1], szq[slot]}
+                              : Taps<V>{szq[0], szq[1], szq[3], szq[4]};
+        ds[2] = dsum(Sj, c_8);
+        dus = dsum(tmul(U, Sj), c_8);
+      }
+    };
     {
-      const TC* P0 = pk[2];
-      auto ztw = [&](int fld, int e) -> Taps<V> {
-        return {V::load(pk[0] + fld * PL + e), V::load(pk[1] + fld * PL + e),
-                V::load(pk[3] + fld * PL + e), V::load(pk[4] + fld * PL + e)};
-      };
       // own unit (tile point); its strip values are stored at the end of the
       // phase, after every ring load of the phase (a shared store may alias
       // the ring for the compiler, which then keeps later loads behind it)
       V own_sx, own_sy, own_gx, own_gy;
       {
-        h0c = V::load(P0 + F_H0 * PL + ec);
-        const Taps<V> ux = xt(P0 + F_U * PL, ec, uc[0]);
+        V ucx;
+        const Taps<V> ux = xt(P0 + F_U * PL, ec, ucx);
         const Taps<V> uy = yt(P0 + F_U * PL, ec), vy = yt(P0 + F_V * PL, ec);
         ux_c = ux;
         uy_c = uy;
         vy_c = vy;
-        uc[1] = V::load(P0 + F_V * PL + ec);
-        uc[2] = V::load(P0 + F_W * PL + ec);
-#pragma unroll
-        for (int c = 0; c < 5; ++c)
-          if (c != 3) fc[c] = V::load(P0 + cons_field(c) * PL + ec);
-        fc[3] = fc[0] * uc[2];
-#pragma unroll
-        for (int c = 0; c < 5; ++c) fcc[c] = fc[c];
-        if constexpr (KEEP) {
-          pc = V::load(P0 + F_P * PL + ec);
-          fcc[4] = c_ig1 * pc;
-        }
-        const Taps<V> uz = ztw(F_U, ec), vz = ztw(F_V, ec), wz = ztw(F_W, ec);
+        const Taps<V> uz = zt(F_U), vz = zt(F_V), wz = zt(F_W);
         const V dxu = c_inv12h * dsum(ux, c_8);
         const V dyv = c_inv12h * dsum(vy, c_8);
         const V dzw = c_inv12h * dsum(wz, c_8);
@@ -609,56 +751,9 @@ __device__ __forceinline__ void stage_tile(const Problem& P, const StageArgs& S,
         const V ezvw = dsum(tmul(vz, wz), c_8);
         own_gx = c_2 * c_inv12h * (eyuv + ezuw);
         own_gy = c_2 * c_inv12h * ezvw;
-
-        // z-direction terms (j = 2)
-        const Taps<V>& U = wz;
-        const Taps<V> aU = tscale(c_alpha, U);
-        const Taps<V> Pt = ztw(F_P, ec);
-        V dFz[5];
-        Taps<V> F0z, F4z, Fmz[3];
-#pragma unroll
-        for (int c = 0; c < 5; ++c) {
-          const Taps<V> F = c == 3 ? tmul(F0z, U)
-                                   : ((KEEP && c == 4) ? tscale(c_ig1, Pt) : ztw(cons_field(c), ec));
-          const V dF = dsum(F, c_8);
-          dFz[c] = dF;
-          if (c == 0) F0z = F;
-          if constexpr (XTRA) {
-            if (c == 4) F4z = F;
-          }
-          if constexpr (KEEP) {
-            if (c >= 1 && c <= 3) Fmz[c - 1] = F;
-          }
-          udf[c] = uc[2] * dF;
-          if (c == 0) continue;
-          Taps<V> g;
-          if (c == 3) g = tfma(aU, F, Pt);                      // a w rho w + p
-          else if (c == 4 && !KEEP) g = tmul(U, taxpy(c_alpha, F, Pt));  // w (a rho E + p)
-          else g = tmul(aU, F);
-          suf[c] = dsum(g, c_8);
-          if (c == 3) suf[0] = c_alpha * dF;  // D_z(rho w)
-        }
-        if constexpr (XTRA) {
-          const Taps<V> UZall[3] = {uz, vz, wz};
-          kgp_extra<!FEIER>(2, U, UZall, F0z, F4z, dFz, fcc, uc, c_8, kx);
-          if constexpr (KEEP) keep_extra(2, U, UZall, Fmz, Pt, dFz, fc, uc, pc, c_8, c_4, kx);
-        }
-        const Taps<V>* UZ[3] = {&uz, &vz, &wz};
-#pragma unroll
-        for (int i = 0; i < 3; ++i) {
-          const V d2 = d2sum(*UZ[i], uc[i], c_16, c_m30);
-          d2u[i] = i == 2 ? c_43 * d2 : d2;
-          if constexpr (DIAG) grad[i][2] = dsum(*UZ[i], c_8);
-        }
-        {
-          const Taps<V> H = tfma(tscale(c_nu6, U), U, ztw(F_H0, ec));
-          const V Hc = fma(c_nu6 * uc[2], uc[2], h0c);
-          d2h = d2sum(H, Hc, c_16, c_m30);
-        }
-        {
-          const Taps<V> Sj = {szq[0], szq[1], szq[3], szq[4]};
-          ds[2] = dsum(Sj, c_8);
-          dus = dsum(tmul(U, Sj), c_8);
+        if constexpr (!ZQ) {
+          centre_values(ucx);
+          z_terms();
         }
       }
       // halo strips: x-halo units need s_x and G_x, y-halo units s_y and G_y
@@ -690,9 +785,13 @@ __device__ __forceinline__ void stage_tile(const Problem& P, const StageArgs& S,
     }
     __syncthreads();
 
-    // ---- phase B: x- and y-direction terms of the own unit, assembly, epilogue
+    // ---- phase B: (z-direction terms from the register queue,) x- and
+    // y-direction terms of the own unit, assembly, epilogue
     if (active_xy) {
-      const TC* P0 = pk[2];
+      if constexpr (ZQ) {
+        centre_values(zc(F_U));
+        z_terms();
+      }
       // the epilogue's Q_in of the own unit at plane k (see qin_raw), issued
       // here so that its latency hides behind the x/y terms
       if constexpr (EPI == EPI_RK) {
@@ -704,6 +803,10 @@ __device__ __forceinline__ void stage_tile(const Problem& P, const StageArgs& S,
           if (!qin_fc) {
 #pragma unroll
             for (int c = 0; c < 5; ++c)
+              qin_raw[c] = IO::load(q_in + (long long)(k + zg) * nn + c * fsq + tile_off);
+          } else if constexpr (QM_GLOBAL) {
+#pragma unroll
+            for (int c = 1; c < 4; ++c)
               qin_raw[c] = IO::load(q_in + (long long)(k + zg) * nn + c * fsq + tile_off);
           }
         }
@@ -718,13 +821,18 @@ __device__ __forceinline__ void stage_tile(const Problem& P, const StageArgs& S,
         const Taps<V> aU = tscale(c_alpha, U);
         const Taps<V> Pt = tap(F_P);
         const Taps<V> Wt = tap(F_W);
+        Taps<V> Uall[3];
+#pragma unroll
+        for (int i = 0; i < 3; ++i)
+          Uall[i] = (i == j) ? U : (i == 2 ? Wt : ((j == 1 && i == 0) ? uy_c : tap(F_U + i)));
         V dFj[5];
         Taps<V> F0j, F4j, Fmj[3];
         // conserved components: D_j f_c, a D_j(u_j f_c) with merged pressure
 #pragma unroll
         for (int c = 0; c < 5; ++c) {
           const Taps<V> F = c == 3 ? tmul(F0j, Wt)
-                                   : ((KEEP && c == 4) ? tscale(c_ig1, Pt) : tap(cons_field(c)));
+                            : (c == 1 || c == 2) ? tmul(F0j, Uall[c - 1])
+                            : ((KEEP && c == 4) ? tscale(c_ig1, Pt) : tap(cons_field(c)));
           const V dF = dsum(F, c_8);
           dFj[c] = dF;
           if (c == 0) F0j = F;
@@ -743,10 +851,6 @@ __device__ __forceinline__ void stage_tile(const Problem& P, const StageArgs& S,
           suf[c] = suf[c] + dsum(g, c_8);
           if (c == 1 + j) suf[0] = fma(c_alpha, dF, suf[0]);  // D_j(rho u_j)
         }
-        Taps<V> Uall[3];
-#pragma unroll
-        for (int i = 0; i < 3; ++i)
-          Uall[i] = (i == j) ? U : (i == 2 ? Wt : ((j == 1 && i == 0) ? uy_c : tap(F_U + i)));
         if constexpr (XTRA) kgp_extra<!FEIER>(j, U, Uall, F0j, F4j, dFj, fcc, uc, c_8, kx);
         if constexpr (KEEP) keep_extra(j, U, Uall, Fmj, Pt, dFj, fc, uc, pc, c_8, c_4, kx);
         // velocity second derivatives (and first derivatives for diagnostics)
@@ -839,7 +943,7 @@ __device__ __forceinline__ void stage_tile(const Problem& P, const StageArgs& S,
           TA qtn[NP], qo[NP], qin[NP], qold[NP], rc[NP];
           if constexpr (QIN_FC) {
             if (qin_fc) {
-              if (c == 3) raw_elems<TA, NP>(qw_q[2], qin);
+              if (c >= 1 && c <= 3) raw_elems<TA, NP>(QM_GLOBAL ? qin_raw[c] : qm_q[2][c - 1], qin);
               else {
 #pragma unroll
                 for (int e = 0; e < NP; ++e) qin[e] = cvt<TA>(fc[c].get(e));
@@ -876,6 +980,7 @@ __device__ __forceinline__ void stage_tile(const Problem& P, const StageArgs& S,
         }
       }
     }
+   }
   }
 
   if constexpr (DIAG) {
@@ -900,13 +1005,13 @@ __device__ __forceinline__ void stage_tile(const Problem& P, const StageArgs& S,
 // arithmetic (128 registers per thread; its shared memory allows two CTAs,
 // and 16 warps per SM run the pure-half stage about 20% faster than 8),
 // otherwise one (the FP32/FP64 ring allows one CTA per SM).
-template <class TC> constexpr int stage_min_blocks() {
+template <class TC, int TX, int TY, int NP> constexpr int stage_min_blocks() {
   return std::is_same<TC, __half>::value ? 2 : 1;
 }
 
 template <class TS, class TT, class TC, class TA, int TX, int TY, int NP, int EPI, bool DIAG,
           int SPL = SPL_QUAD, int RKF = RKF_RUNTIME>
-__global__ void __launch_bounds__(Geo<TX, TY, NP>::NT, stage_min_blocks<TC>())
+__global__ void __launch_bounds__(Geo<TX, TY, NP>::NT, stage_min_blocks<TC, TX, TY, NP>())
 stage_kernel(const Problem P, const StageArgs S) {
   const long long cta = ((long long)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
   stage_tile<TS, TT, TC, TA, TX, TY, NP, EPI, DIAG, SPL, RKF>(

@@ -96,6 +96,18 @@ __device__ __forceinline__ Vec<__half, 2> fma(Vec<__half, 2> a, Vec<__half, 2> b
 }
 __device__ __forceinline__ Vec<__half, 2> rcp(Vec<__half, 2> a) { return Vec<__half, 2>(h2rcp(a.v)); }
 
+// pin(v): an empty assembly statement that makes the value opaque to the
+// compiler.  The stage kernel passes the register-queue taps through it: with
+// the z march unrolled, the compiler otherwise rewrites some paired-FP32
+// arithmetic on values it can relate across unrolled planes and rounds it
+// differently in different copies of the loop body (results then depend on
+// the z-chunk position; measured, 1 ulp), whereas every kernel must compute
+// each grid point with the same operations in the same order.
+template <class T, int NP> __device__ __forceinline__ void pin(Vec<T, NP>&) {}
+__device__ __forceinline__ void pin(Vec<float, 2>& a) {
+  asm volatile("" : "+f"(a.v.x), "+f"(a.v.y));
+}
+
 // ---------------------------------------------------- storage <-> compute units
 // Load NP consecutive storage elements and convert to the compute type.
 template <class TC, int NP, class TS> struct UnitIO;
