@@ -53,18 +53,46 @@ template <> struct Vec<float, 2> {
   static __device__ __forceinline__ Vec mix(const Vec& a, const Vec& b) { return Vec(a.v.y, b.v.x); }
   __device__ __forceinline__ Vec swapped() const { return Vec(v.y, v.x); }
 };
+// The paired operations are written as PTX with an explicit rounding mode
+// (add/sub/mul/fma .rn .f32x2): an explicit rounding mode forbids the code
+// generator to fuse a multiply into a following add, so every kernel that
+// evaluates the same expression rounds it the same way, whatever the
+// surrounding code (the CUDA paired intrinsics were fused in some code shapes
+// and not in others, and results then differed in the last bit between
+// kernels that compute the same grid point).
+#define TGV_F32X2_OP2(NAME, OP)                                                         \
+  __device__ __forceinline__ float2 NAME(float2 a, float2 b) {                           \
+    float2 d;                                                                            \
+    asm("{ .reg .b64 ra, rb, rd; mov.b64 ra, {%2, %3}; mov.b64 rb, {%4, %5}; " OP        \
+        " rd, ra, rb; mov.b64 {%0, %1}, rd; }"                                           \
+        : "=f"(d.x), "=f"(d.y)                                                           \
+        : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));                                       \
+    return d;                                                                            \
+  }
+TGV_F32X2_OP2(f32x2_add, "add.rn.f32x2")
+TGV_F32X2_OP2(f32x2_sub, "sub.rn.f32x2")
+TGV_F32X2_OP2(f32x2_mul, "mul.rn.f32x2")
+#undef TGV_F32X2_OP2
+__device__ __forceinline__ float2 f32x2_fma(float2 a, float2 b, float2 c) {
+  float2 d;
+  asm("{ .reg .b64 ra, rb, rc, rd; mov.b64 ra, {%2, %3}; mov.b64 rb, {%4, %5}; "
+      "mov.b64 rc, {%6, %7}; fma.rn.f32x2 rd, ra, rb, rc; mov.b64 {%0, %1}, rd; }"
+      : "=f"(d.x), "=f"(d.y)
+      : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y), "f"(c.x), "f"(c.y));
+  return d;
+}
 __device__ __forceinline__ Vec<float, 2> operator+(Vec<float, 2> a, Vec<float, 2> b) {
-  return Vec<float, 2>(__fadd2_rn(a.v, b.v));
+  return Vec<float, 2>(f32x2_add(a.v, b.v));
 }
 __device__ __forceinline__ Vec<float, 2> operator-(Vec<float, 2> a) { return Vec<float, 2>(-a.v.x, -a.v.y); }
 __device__ __forceinline__ Vec<float, 2> operator-(Vec<float, 2> a, Vec<float, 2> b) {
-  return Vec<float, 2>(__fadd2_rn(a.v, make_float2(-b.v.x, -b.v.y)));
+  return Vec<float, 2>(f32x2_sub(a.v, b.v));
 }
 __device__ __forceinline__ Vec<float, 2> operator*(Vec<float, 2> a, Vec<float, 2> b) {
-  return Vec<float, 2>(__fmul2_rn(a.v, b.v));
+  return Vec<float, 2>(f32x2_mul(a.v, b.v));
 }
 __device__ __forceinline__ Vec<float, 2> fma(Vec<float, 2> a, Vec<float, 2> b, Vec<float, 2> c) {
-  return Vec<float, 2>(__ffma2_rn(a.v, b.v, c.v));
+  return Vec<float, 2>(f32x2_fma(a.v, b.v, c.v));
 }
 __device__ __forceinline__ Vec<float, 2> rcp(Vec<float, 2> a) {
   return Vec<float, 2>(__frcp_rn(a.v.x), __frcp_rn(a.v.y));
@@ -97,12 +125,11 @@ __device__ __forceinline__ Vec<__half, 2> fma(Vec<__half, 2> a, Vec<__half, 2> b
 __device__ __forceinline__ Vec<__half, 2> rcp(Vec<__half, 2> a) { return Vec<__half, 2>(h2rcp(a.v)); }
 
 // pin(v): an empty assembly statement that makes the value opaque to the
-// compiler.  The stage kernel passes the register-queue taps through it: with
-// the z march unrolled, the compiler otherwise rewrites some paired-FP32
-// arithmetic on values it can relate across unrolled planes and rounds it
-// differently in different copies of the loop body (results then depend on
-// the z-chunk position; measured, 1 ulp), whereas every kernel must compute
-// each grid point with the same operations in the same order.
+// compiler.  The stage kernel passes its register-queue taps through it.
+// Without it the register-queue kernel and the shared-memory-ring kernel,
+// which apply the same operations to the same values, differed in the last
+// bit at rare grid points (measured: first after 320 steps of a 32^3 run);
+// with it they agree bit for bit (the ensemble and slab tests compare them).
 template <class T, int NP> __device__ __forceinline__ void pin(Vec<T, NP>&) {}
 __device__ __forceinline__ void pin(Vec<float, 2>& a) {
   asm volatile("" : "+f"(a.v.x), "+f"(a.v.y));
