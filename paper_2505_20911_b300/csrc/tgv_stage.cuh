@@ -36,10 +36,12 @@
 //   1. primitives of the prefetched plane zl -> ring slot            | barrier
 //   2. prefetch plane zl+1 (and the next centre plane's Qt); D_x u + D_y v
 //      of plane zl (z-taps of s_z); centre plane k = zl-2: s_x, s_y and the
-//      mixed-derivative fields on the tile and its x/y halo strips, and
-//      every z-direction term of the thread's unit                   | barrier
-//   3. the x- and y-direction terms at plane k (centre plane and strips
-//      only), assembly of R, RK epilogue.
+//      mixed-derivative fields on the tile and its x/y halo strips (and,
+//      when the z taps come from the ring, every z-direction term of the
+//      thread's unit)                                                | barrier
+//   3. (the z-direction terms, when the thread's z taps come from its
+//      register queue,) the x- and y-direction terms at plane k (centre
+//      plane and strips only), assembly of R, RK epilogue.
 #pragma once
 
 #include "tgv_common.cuh"
