@@ -1,7 +1,7 @@
 // tgv_vec.cuh - a "unit" of NP consecutive x points handled by one thread.
 //
 // Vec<T, 1> is a scalar; Vec<float, 2> packs two FP32 lanes and uses the
-// sm_100+ paired FP32 intrinsics (__fadd2_rn, __fmul2_rn, __ffma2_rn), which
+// sm_100+ paired FP32 operations (PTX add/sub/mul/fma .rn .f32x2), which
 // issue once for both lanes; Vec<__half, 2> is __half2.  All stencil arithmetic of the
 // stage kernel is written once against this interface.
 #pragma once
