@@ -1,0 +1,76 @@
+"""The FP32-arithmetic stage kernel of the 32x16 tile keeps each thread's z taps
+in a register queue and marches in z with its loop unrolled by the ring depth
+(five planes); the other kernels (the fused-diagnostics stage, the ensemble, the
+other split families, the smaller tiles) read the same taps from the shared-memory
+ring.  These tests check the queue path where it can go wrong: every z-chunk
+length (every remainder of the unrolled loop and every position of the chunk
+start in it) gives the same residual and the same steps bit for bit, the result
+matches the oracle to FP32 rounding, and the queue and ring paths agree bit for
+bit."""
+import pytest
+import torch
+
+import oracle
+import paper_2505_20911_b300 as tgv
+from _util import decode, encode, max_rel, oracle_flow, random_state
+
+pytestmark = pytest.mark.gpu
+
+# every remainder modulo the ring depth, chunks shorter than the ring, and one
+# chunk for the whole box (n = 40: the 32x16 tile leaves ragged tiles in x and y)
+ZCHUNKS = [1, 2, 3, 4, 5, 6, 7, 11, 13, 40]
+
+
+@pytest.mark.parametrize("mode", ["fp32", "hpsp", "fp16_fp32"])
+def test_residual_independent_of_zchunk(mode):
+    enc = "offset" if mode == "fp16_fp32" else "plain"
+    cfg = tgv.Config(n=40, mode=mode, tile=1, mach=0.3, re=100.0, encoding=enc)
+    qs = encode(cfg, random_state(cfg, seed=41))
+    ref = None
+    for zc in [0] + ZCHUNKS:
+        r = torch.empty(5, 40, 40, 40, dtype=cfg.compute_dtype, device="cuda")
+        tgv.rhs_eval(cfg.with_(zchunk=zc), qs, r)
+        if ref is None:
+            ref = r.clone()
+            # FP32 arithmetic on the stored state: within FP32 rounding of the
+            # oracle (the study's bound for these modes, measured ~3e-7)
+            err = max(max_rel(r.double().cpu(), oracle.residual(oracle_flow(cfg), decode(cfg, qs))))
+            assert err < 5e-6, err
+        else:
+            assert torch.equal(r, ref), zc
+
+
+@pytest.mark.parametrize("mode", ["fp32", "hpsp"])
+def test_rk_step_independent_of_zchunk(mode):
+    cfg = tgv.Config(n=40, mode=mode, tile=1, mach=0.3, re=100.0)
+    q0 = encode(cfg, random_state(cfg, seed=43))
+    ref = None
+    for zc in [0] + ZCHUNKS:
+        c = cfg.with_(zchunk=zc)
+        qa, qb, qt = q0.clone(), torch.empty_like(q0), tgv.empty_qt(c)
+        par = tgv.rk_step(c, qa, qb, qt, 0.002, 3)
+        out = (qb if par else qa).clone()
+        if ref is None:
+            ref = out
+        else:
+            assert torch.equal(out, ref), zc
+
+
+def test_register_queue_matches_ring_path():
+    """rk_step's stages run the register-queue kernel; with diagnostics after
+    every step, each step's first stage runs the fused-diagnostics kernel,
+    which reads its z taps from the ring.  The states agree bit for bit."""
+    cfg = tgv.Config(n=48, mode="hpsp", tile=1, re=400.0)
+    q0 = tgv.empty_state(cfg)
+    tgv.tgv_init(cfg, q0)
+    outs = []
+    for diag_every in (0, 1):
+        qa, qb, qt = q0.clone(), torch.empty_like(q0), tgv.empty_qt(cfg)
+        kw = {}
+        if diag_every:
+            kw = {"diag": torch.zeros(21 * tgv.TGV_DIAG_COUNT, dtype=torch.float64, device="cuda"),
+                  "workspace": torch.empty(tgv.tgv_workspace_bytes(cfg), dtype=torch.uint8,
+                                           device="cuda")}
+        par = tgv.rk_step(cfg, qa, qb, qt, 0.003, 20, diag_every, **kw)
+        outs.append((qb if par else qa).clone())
+    assert torch.equal(outs[0], outs[1])
