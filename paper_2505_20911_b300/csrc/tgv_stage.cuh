@@ -126,24 +126,13 @@ struct Geo {
   static constexpr int PERH = (HU + NT - 1) / NT;
 };
 
-// Raw-plane staging depth: with FP32 arithmetic on 16-bit storage, four
-// staged raw planes are kept (7 KB each for a 32x16 tile), so the RK epilogue
-// of centre plane k reads its own unit's Q_in from the staging of plane k
-// (staged three planes earlier and not yet overwritten); otherwise one.  (Four
-// FP32 planes would take the CTA to 220 KB of shared memory and leave the L1
-// cache too small for the cp.async traffic: measured 15% slower.)
-template <class TS, class TC>
-__host__ __device__ constexpr int raw_slots() {
-  return std::is_same<TC, float>::value && sizeof(TS) == 2 ? 4 : 1;
-}
-
 // Shared memory: ring, strips (compute type), then the cp.async staging of
 // the raw planes (storage type) and one raw Qt plane of the tile.
 template <class TS, class TT, class TC, int TX, int TY, int NP>
 constexpr size_t stage_smem_bytes() {
   using G = Geo<TX, TY, NP>;
   return sizeof(TC) * ((size_t)NSLOT * NFLD * G::PL + (size_t)NSTRIP * G::PL) +
-         sizeof(TS) * NP * 5 * (size_t)G::PLU * raw_slots<TS, TC>() +
+         sizeof(TS) * NP * 5 * (size_t)G::PLU +
          sizeof(TT) * NP * 5 * (size_t)G::NT;
 }
 // Largest dynamic shared memory a stage CTA may request (B300: 227 KB per CTA,
@@ -297,12 +286,12 @@ __device__ __forceinline__ void stage_tile(const Problem& P, const StageArgs& S,
   // left/right columns of rows 2..TY+1, rows TY+2..TY+3).
   using RawS = typename UnitIO<TC, NP, TS>::Raw;
   using RawT = typename UnitIO<TA, NP, TT>::Raw;
-  constexpr int RS = raw_slots<TS, TC>();
-  RawS* stage_q = reinterpret_cast<RawS*>(strips + NSTRIP * PL);       // [RS][5][PLU]
-  RawT* stage_t = reinterpret_cast<RawT*>(stage_q + RS * 5 * PLU);    // [5][NT]
+  RawS* stage_q = reinterpret_cast<RawS*>(strips + NSTRIP * PL);       // [5][PLU]
+  RawT* stage_t = reinterpret_cast<RawT*>(stage_q + 5 * PLU);         // [5][NT]
   const int zbase = z0 - 2;
-  // staging slot of raw plane zl (RS is a power of two)
-  auto raw_plane = [&](int zl) -> RawS* { return stage_q + ((zl - zbase) & (RS - 1)) * 5 * PLU; };
+  // one staging plane: the next raw plane is copied into it after every thread
+  // has converted the current one (the commit precedes the CTA barrier)
+  auto raw_plane = [&](int) -> RawS* { return stage_q; };
   // Global addresses are formed as a CTA-uniform 64-bit base (plane,
   // component) plus a 32-bit per-thread offset within the plane (n <= 1024).
   unsigned goff[PERU];
@@ -371,12 +360,13 @@ __device__ __forceinline__ void stage_tile(const Problem& P, const StageArgs& S,
       cp_async<sizeof(RawT)>(dst + c * NT + tid, qt + (long long)kq * nn + c * fst + tile_off);
   };
   // The epilogue's Q_in of the own unit, in storage precision:
-  //  - four raw planes staged (raw_slots): read from the staging of its plane;
   //  - FP32 storage and arithmetic, plain encoding: rho and rho E of the
   //    centre plane are already in registers as exact copies of the stored
-  //    values (fc below); the momenta, which the ring does not hold, are
-  //    carried from the plane loader in a three-plane register queue (planes
-  //    zl, zl-1, zl-2; zeroed first, so no entry is read before it is written);
+  //    values (fc below); the momenta, which the ring does not hold, come from
+  //    global memory in the register-queue kernels (QM_GLOBAL) and otherwise
+  //    from a three-plane register queue of the raw values carried from the
+  //    plane loader (planes zl, zl-1, zl-2; zeroed first, so no entry is read
+  //    before it is written);
   //  - otherwise: re-read from global memory at the start of phase B (a cache
   //    hit: the loader read it two planes earlier).
   constexpr bool QIN_FC = std::is_same<TS, float>::value && std::is_same<TC, float>::value;
@@ -797,11 +787,7 @@ __device__ __forceinline__ void stage_tile(const Problem& P, const StageArgs& S,
       // the epilogue's Q_in of the own unit at plane k (see qin_raw), issued
       // here so that its latency hides behind the x/y terms
       if constexpr (EPI == EPI_RK) {
-        if constexpr (RS > 1) {
-          const RawS* src = raw_plane(k);
-#pragma unroll
-          for (int c = 0; c < 5; ++c) qin_raw[c] = src[c * PLU + tid];
-        } else {
+        {
           if (!qin_fc) {
 #pragma unroll
             for (int c = 0; c < 5; ++c)
