@@ -56,11 +56,17 @@ def test_rk_step_independent_of_zchunk(mode):
             assert torch.equal(out, ref), zc
 
 
-def test_register_queue_matches_ring_path():
+@pytest.mark.parametrize("symmetric", [False, True])
+def test_register_queue_matches_ring_path(symmetric):
     """rk_step's stages run the register-queue kernel; with diagnostics after
     every step, each step's first stage runs the fused-diagnostics kernel,
-    which reads its z taps from the ring.  The states agree bit for bit."""
-    cfg = tgv.Config(n=48, mode="hpsp", tile=1, re=400.0)
+    which reads its z taps from the ring.  The states agree bit for bit, in
+    the periodic box and in the symmetric box (mirror ghosts at the z faces)."""
+    if symmetric:
+        cfg = tgv.Config(n=48, mode="hpsp", tile=1, length=3.141592653589793, symmetric=True,
+                         mach=0.5, re=800.0)
+    else:
+        cfg = tgv.Config(n=48, mode="hpsp", tile=1, re=400.0)
     q0 = tgv.empty_state(cfg)
     tgv.tgv_init(cfg, q0)
     outs = []
