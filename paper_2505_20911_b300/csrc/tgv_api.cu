@@ -279,6 +279,8 @@ static int32_t launch_stage_common(const tgv_config* cfg, const StageArgs& S, bo
     const int i = !S.read_qt ? 0 : (S.write_qt ? 1 : 2);
     fn = L.stage_rk[i][tile];
   }
+  if (!rhs && S.diag_part && v == SPL_QUAD && S.scaled_qt && !S.read_qt && S.write_qt)
+    fn = L.stage_rk_diag[tile];
   if (!fn) return TGV_ERR_UNSUPPORTED;
   cudaError_t e = fn(P, A, zc, st);
   return e == cudaSuccess ? TGV_OK : TGV_ERR_CUDA;

@@ -54,6 +54,7 @@ struct ModeLaunchers {
   StageFn stage[NUM_SPL][NUM_TILES];      // EPI_RK (null where a mode does not build it)
   StageFn stage_rk[3][NUM_TILES];         // EPI_RK, quadratic split, flags RKF_STAGE(i)
   StageFn stage_diag[NUM_SPL][NUM_TILES]; // EPI_RK with the fused diagnostics of its input
+  StageFn stage_rk_diag[NUM_TILES];       // rk_step's first stage with the fused diagnostics
   StageFn rhs[NUM_SPL][NUM_TILES];        // EPI_RHS
   OccFn occupancy[NUM_TILES];    // resident CTAs per SM of the EPI_RK kernel
   size_t smem[NUM_TILES];        // dynamic shared memory per CTA
@@ -96,6 +97,17 @@ cudaError_t launch_stage_rk(const Problem& P, const StageArgs& S, int zchunk, cu
     return launch_stage<TS, TT, TC, TA, TX, TY, NP, EPI_RK, false, SPL_QUAD>(P, S, zchunk, st);
   return launch_stage<TS, TT, TC, TA, TX, TY, NP, EPI_RK, false, SPL_QUAD, RKF_STAGE(I)>(P, S, zchunk,
                                                                                        st);
+}
+
+// rk_step's first stage of a logged step: the fused-diagnostics kernel with the
+// flags of stage 0 built in (as launch_stage_rk).
+template <class TS, class TT, class TC, class TA, int TX, int TY, int NP>
+cudaError_t launch_stage_rk_diag(const Problem& P, const StageArgs& S, int zchunk, cudaStream_t st) {
+  constexpr bool QIN_FC = std::is_same<TS, float>::value && std::is_same<TC, float>::value;
+  if (QIN_FC && P.encoding != TGV_ENC_PLAIN)
+    return launch_stage<TS, TT, TC, TA, TX, TY, NP, EPI_RK, true, SPL_QUAD>(P, S, zchunk, st);
+  return launch_stage<TS, TT, TC, TA, TX, TY, NP, EPI_RK, true, SPL_QUAD, RKF_STAGE(0)>(P, S, zchunk,
+                                                                                      st);
 }
 
 template <class TS, class TT, class TC, class TA, int TX, int TY, int NP>
@@ -143,6 +155,7 @@ void set_tile(ModeLaunchers& L, int t) {
   L.stage_rk[0][t] = launch_stage_rk<TS, TT, TC, TA, TX, TY, NP, 0>;
   L.stage_rk[1][t] = launch_stage_rk<TS, TT, TC, TA, TX, TY, NP, 1>;
   L.stage_rk[2][t] = launch_stage_rk<TS, TT, TC, TA, TX, TY, NP, 2>;
+  L.stage_rk_diag[t] = launch_stage_rk_diag<TS, TT, TC, TA, TX, TY, NP>;
   if constexpr (WITH_KGP) {
     set_split<TS, TT, TC, TA, TX, TY, NP, SPL_KGP>(L, t);
     set_split<TS, TT, TC, TA, TX, TY, NP, SPL_KEEP>(L, t);

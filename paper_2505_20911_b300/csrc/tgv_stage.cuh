@@ -379,10 +379,11 @@ __device__ __forceinline__ void stage_tile(const Problem& P, const StageArgs& S,
   // register queues are never shifted.  Only the 32x16 tile: the smaller
   // tiles hold two region units per thread and would spill (their FP32
   // kernel serves the FP64-state mode, two CTAs per SM).  Not in the
-  // fused-diagnostics stage and the ensemble's persistent kernel, whose extra
-  // live values would then spill.  Either path computes the same values.
+  // fused-diagnostics stage with run-time RK flags and the ensemble's
+  // persistent kernel, whose extra live values would then spill.  Either
+  // path computes the same values.
   constexpr bool ZQ = std::is_same<TC, float>::value && NP == 2 && NT >= 256 && SPL == SPL_QUAD &&
-                      !DIAG && !(RKF != RKF_RUNTIME && (RKF & RKF_ENC_RT));
+                      !(DIAG && RKF == RKF_RUNTIME) && !(RKF != RKF_RUNTIME && (RKF & RKF_ENC_RT));
   V zq[ZQ ? NSLOT : 1][NF];
 #pragma unroll
   for (int d = 0; d < (ZQ ? 5 : 1); ++d)

@@ -1,12 +1,12 @@
 """The FP32-arithmetic stage kernel of the 32x16 tile keeps each thread's z taps
 in a register queue and marches in z with its loop unrolled by the ring depth
-(five planes); the other kernels (the fused-diagnostics stage, the ensemble, the
-other split families, the smaller tiles) read the same taps from the shared-memory
-ring.  These tests check the queue path where it can go wrong: every z-chunk
+(five planes); the other kernels (the fused-diagnostics stage with run-time RK
+flags, the ensemble, the other split families, the smaller tiles) read the same
+taps from the shared-memory ring.  These tests check the queue path where it can go wrong: every z-chunk
 length (every remainder of the unrolled loop and every position of the chunk
 start in it) gives the same residual and the same steps bit for bit, the result
 matches the oracle to FP32 rounding, and the queue and ring paths agree bit for
-bit."""
+bit (here and, for the ensemble's ring-path kernel, in test_gpu_ensemble.py)."""
 import pytest
 import torch
 
@@ -58,15 +58,17 @@ def test_rk_step_independent_of_zchunk(mode):
 
 @pytest.mark.parametrize("symmetric", [False, True])
 def test_register_queue_matches_ring_path(symmetric):
-    """rk_step's stages run the register-queue kernel; with diagnostics after
-    every step, each step's first stage runs the fused-diagnostics kernel,
-    which reads its z taps from the ring.  The states agree bit for bit, in
-    the periodic box and in the symmetric box (mirror ghosts at the z faces)."""
+    """With the offset encoding of the FP32 state, rk_step's stages run the
+    run-time-flag kernels: the plain stages keep their z taps in the register
+    queue, while the fused-diagnostics stage (the first stage of every step
+    when diagnostics are logged after every step) reads them from the ring.
+    The states agree bit for bit, in the periodic box and in the symmetric box
+    (mirror ghosts at the z faces)."""
     if symmetric:
         cfg = tgv.Config(n=48, mode="hpsp", tile=1, length=3.141592653589793, symmetric=True,
-                         mach=0.5, re=800.0)
+                         mach=0.5, re=800.0, encoding="offset")
     else:
-        cfg = tgv.Config(n=48, mode="hpsp", tile=1, re=400.0)
+        cfg = tgv.Config(n=48, mode="hpsp", tile=1, re=400.0, encoding="offset")
     q0 = tgv.empty_state(cfg)
     tgv.tgv_init(cfg, q0)
     outs = []
