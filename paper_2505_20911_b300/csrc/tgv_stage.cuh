@@ -370,7 +370,7 @@ __device__ __forceinline__ void stage_tile(const Problem& P, const StageArgs& S,
   //  - otherwise: re-read from global memory at the start of phase B (a cache
   //    hit: the loader read it two planes earlier).
   constexpr bool QIN_FC = std::is_same<TS, float>::value && std::is_same<TC, float>::value;
-  // Own-unit z taps from registers (FP32 arithmetic, quadratic splits): the
+  // Own-unit z taps from registers (FP32 or FP16 arithmetic, quadratic splits): the
   // loader keeps the primitives of its own unit for the last five planes
   // (zq[s][field] holds the plane committed to ring slot s), so the
   // z-direction terms read no shared memory; the ring still serves the x and
@@ -382,7 +382,8 @@ __device__ __forceinline__ void stage_tile(const Problem& P, const StageArgs& S,
   // fused-diagnostics stage with run-time RK flags and the ensemble's
   // persistent kernel, whose extra live values would then spill.  Either
   // path computes the same values.
-  constexpr bool ZQ = std::is_same<TC, float>::value && NP == 2 && NT >= 256 && SPL == SPL_QUAD &&
+  constexpr bool ZQ = (std::is_same<TC, float>::value || std::is_same<TC, __half>::value) &&
+                      NP == 2 && NT >= 256 && SPL == SPL_QUAD &&
                       !(DIAG && RKF == RKF_RUNTIME) && !(RKF != RKF_RUNTIME && (RKF & RKF_ENC_RT));
   V zq[ZQ ? NSLOT : 1][NF];
 #pragma unroll

@@ -134,6 +134,11 @@ template <class T, int NP> __device__ __forceinline__ void pin(Vec<T, NP>&) {}
 __device__ __forceinline__ void pin(Vec<float, 2>& a) {
   asm volatile("" : "+f"(a.v.x), "+f"(a.v.y));
 }
+__device__ __forceinline__ void pin(Vec<__half, 2>& a) {
+  unsigned r = *reinterpret_cast<unsigned*>(&a.v);
+  asm volatile("" : "+r"(r));
+  a.v = *reinterpret_cast<__half2*>(&r);
+}
 
 // ---------------------------------------------------- storage <-> compute units
 // Load NP consecutive storage elements and convert to the compute type.
