@@ -397,7 +397,8 @@ __device__ __forceinline__ void stage_tile(const Problem& P, const StageArgs& S,
   const bool qin_fc = QIN_FC && (RK_CT && !(RKF & RKF_ENC_RT) ? (RKF & RKF_PLAIN) != 0
                                                               : P.encoding == TGV_ENC_PLAIN);
   RawS qin_raw[5];
-  // raw rho u, rho v, rho w: of ring slot s (ZQ), else of planes zl, zl-1, zl-2
+  // raw rho u, rho v, rho w of planes zl, zl-1, zl-2 (ring-path kernels; the
+  // register-queue kernels re-read the momenta from global memory)
   constexpr bool QM_GLOBAL = ZQ;  // momenta re-read from global memory
   constexpr int NQM = QIN_FC && !QM_GLOBAL ? 3 : 1;
   RawS qm_q[NQM][3];
