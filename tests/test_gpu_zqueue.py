@@ -1,12 +1,13 @@
-"""The FP32-arithmetic stage kernel of the 32x16 tile keeps each thread's z taps
-in a register queue and marches in z with its loop unrolled by the ring depth
+"""The FP32- and FP16-arithmetic stage kernels of the 32x16 tile keep each thread's z taps
+in a register queue and march in z with the loop unrolled by the ring depth
 (five planes); the other kernels (the fused-diagnostics stage with run-time RK
 flags, the ensemble, the other split families, the smaller tiles) read the same
-taps from the shared-memory ring.  These tests check the queue path where it can go wrong: every z-chunk
-length (every remainder of the unrolled loop and every position of the chunk
-start in it) gives the same residual and the same steps bit for bit, the result
-matches the oracle to FP32 rounding, and the queue and ring paths agree bit for
-bit (here and, for the ensemble's ring-path kernel, in test_gpu_ensemble.py)."""
+taps from the shared-memory ring.  These tests check the queue path where it
+can go wrong: every z-chunk length (every remainder of the unrolled loop and
+every position of the chunk start in it) gives the same residual and the same
+steps bit for bit, the result matches the oracle to the rounding of the
+arithmetic, and the queue and ring paths agree bit for bit (here and, for the
+ensemble's ring-path kernel, in test_gpu_ensemble.py)."""
 import pytest
 import torch
 
@@ -21,9 +22,15 @@ pytestmark = pytest.mark.gpu
 ZCHUNKS = [1, 2, 3, 4, 5, 6, 7, 11, 13, 40]
 
 
-@pytest.mark.parametrize("mode", ["fp32", "hpsp", "fp16_fp32"])
+# residual against the oracle on the stored state: FP32 arithmetic within FP32
+# rounding (the study's bound for these modes, measured ~3e-7); FP16
+# arithmetic (half2) within about 20 units of FP16 rounding (measured ~2e-3)
+ORACLE_BOUND = {"fp32": 5e-6, "hpsp": 5e-6, "fp16_fp32": 5e-6, "fp16": 1e-2}
+
+
+@pytest.mark.parametrize("mode", list(ORACLE_BOUND))
 def test_residual_independent_of_zchunk(mode):
-    enc = "offset" if mode == "fp16_fp32" else "plain"
+    enc = "offset" if mode in ("fp16_fp32", "fp16") else "plain"
     cfg = tgv.Config(n=40, mode=mode, tile=1, mach=0.3, re=100.0, encoding=enc)
     qs = encode(cfg, random_state(cfg, seed=41))
     ref = None
@@ -32,17 +39,16 @@ def test_residual_independent_of_zchunk(mode):
         tgv.rhs_eval(cfg.with_(zchunk=zc), qs, r)
         if ref is None:
             ref = r.clone()
-            # FP32 arithmetic on the stored state: within FP32 rounding of the
-            # oracle (the study's bound for these modes, measured ~3e-7)
             err = max(max_rel(r.double().cpu(), oracle.residual(oracle_flow(cfg), decode(cfg, qs))))
-            assert err < 5e-6, err
+            assert err < ORACLE_BOUND[mode], err
         else:
             assert torch.equal(r, ref), zc
 
 
-@pytest.mark.parametrize("mode", ["fp32", "hpsp"])
+@pytest.mark.parametrize("mode", ["fp32", "hpsp", "fp16"])
 def test_rk_step_independent_of_zchunk(mode):
-    cfg = tgv.Config(n=40, mode=mode, tile=1, mach=0.3, re=100.0)
+    cfg = tgv.Config(n=40, mode=mode, tile=1, mach=0.3, re=100.0,
+                     encoding="offset" if mode == "fp16" else "plain")
     q0 = encode(cfg, random_state(cfg, seed=43))
     ref = None
     for zc in [0] + ZCHUNKS:
