@@ -712,6 +712,37 @@ def extra_workloads(args, tgv, torch, dev, stream, peaks):
                        "speedup": direct_ms / graph_ms}
     del qa, qb, qt, graph
 
+    # the z-slab decomposition's own cost on one GPU: the headline 256^3 box as
+    # P slabs on this device (ghost planes exchanged by device copies before
+    # every stage, the P slab-stage launches of a stage one after another)
+    # against the whole box, 20 steps each.  With P ranks each would run one
+    # slab, so (total - exchange) / P estimates a rank's kernel time per step
+    # (transfers not included) and whole / (total - exchange) the strong-scaling
+    # efficiency of the kernels alone.
+    from paper_2505_20911_b300 import slab
+    cfg = mode_config(tgv, 256, HEADLINE)
+    dt256 = DT_DEFAULT
+    local = {}
+    qa = tgv.empty_state(cfg)
+    qb, qt = torch.empty_like(qa), tgv.empty_qt(cfg)
+    tgv.tgv_init(cfg, qa)
+    tgv.rk_step(cfg, qa, qb, qt, dt256, 3, 0, None, None, stream)
+    local["whole_box_ms_per_step"] = ev_time(
+        lambda: tgv.rk_step(cfg, qa, qb, qt, dt256, 20, 0, None, None, stream)) / 20
+    del qa, qb, qt
+    for nslab in (2, 4, 8):
+        dom = slab.SlabDomain(cfg, [slab.slab_bounds(256, nslab, r) for r in range(nslab)])
+        dom.init(stream)
+        dom.step(dt256, 3, stream=stream)
+        tot = ev_time(lambda: dom.step(dt256, 20, stream=stream)) / 20
+        exch = ev_time(lambda: [dom.exchange(stream) for _ in range(60)]) / 20
+        local[f"slabs_{nslab}"] = {"ms_per_step": tot, "exchange_ms_per_step": exch,
+                                   "per_rank_kernel_ms_per_step": (tot - exch) / nslab,
+                                   "kernel_efficiency": local["whole_box_ms_per_step"] / (tot - exch)}
+        del dom
+    torch.cuda.empty_cache()
+    out["slab_local_256"] = local
+
     # adjoint: 64^3, 200 steps, checkpoint every 20
     adj = {}
     for mode in ("fp64", "fp32"):
@@ -895,7 +926,8 @@ def main():
                 roofline_alu=res["roofline_alu"],
                 e2e=res["e2e"], gpu_launches=res["gpu_launches"], clocks=res["clocks"], modes=res["modes"],
                 diag_last=res["diag_last"])
-    for key in ("replicas", "slab", "n512", "tgsym_256", "graph_32", "adjoint_64", "ensemble_48"):
+    for key in ("replicas", "slab", "n512", "tgsym_256", "graph_32", "slab_local_256", "adjoint_64",
+                "ensemble_48"):
         if res.get(key) is not None:
             line[key] = res[key]
     if world == 1 and not args.no_cpu:
