@@ -40,20 +40,23 @@ def slab_bounds(n: int, world: int, rank: int) -> tuple[int, int]:
 
 def ghost_exchange_ops(q, rank: int, world: int, dist):
     """The point-to-point operations of one ghost exchange of a slab state q
-    ((5, nz + 4, N, N), any device): per field, in this order on every rank,
-    send the top two owned planes up, the bottom two down, receive the lower
-    ghosts from below and the upper ghosts from above.  The common order makes
-    the messages pair up correctly also when the two neighbours are the same
-    rank (world = 2)."""
+    ((5, nz + 4, N, N), any device), with the four buffers they use: the top
+    two owned planes of all five fields packed into one block go up, the
+    bottom two down, and one block is received from below (the lower ghosts)
+    and one from above (the upper ghosts) - four messages per rank instead of
+    one per field and direction.  The same order on every rank makes the
+    messages pair up correctly also when the two neighbours are the same rank
+    (world = 2: per peer, messages match in the order they are posted).
+    Returns (ops, recv_lower, recv_upper)."""
+    import torch
     nz = q.shape[1] - 2 * GHOST
     lo, hi = (rank - 1) % world, (rank + 1) % world
-    ops = []
-    for c in range(q.shape[0]):
-        ops.append(dist.P2POp(dist.isend, q[c, nz:nz + GHOST], hi))
-        ops.append(dist.P2POp(dist.isend, q[c, GHOST:2 * GHOST], lo))
-        ops.append(dist.P2POp(dist.irecv, q[c, 0:GHOST], lo))
-        ops.append(dist.P2POp(dist.irecv, q[c, nz + GHOST:nz + 2 * GHOST], hi))
-    return ops
+    up = q[:, nz:nz + GHOST].contiguous()
+    down = q[:, GHOST:2 * GHOST].contiguous()
+    recv_lower, recv_upper = torch.empty_like(up), torch.empty_like(down)
+    ops = [dist.P2POp(dist.isend, up, hi), dist.P2POp(dist.isend, down, lo),
+           dist.P2POp(dist.irecv, recv_lower, lo), dist.P2POp(dist.irecv, recv_upper, hi)]
+    return ops, recv_lower, recv_upper
 
 
 def exchange_ghosts(q, rank: int, world: int, dist=None) -> None:
@@ -68,8 +71,11 @@ def exchange_ghosts(q, rank: int, world: int, dist=None) -> None:
         return
     if dist is None:
         import torch.distributed as dist
-    for req in dist.batch_isend_irecv(ghost_exchange_ops(q, rank, world, dist)):
+    ops, recv_lower, recv_upper = ghost_exchange_ops(q, rank, world, dist)
+    for req in dist.batch_isend_irecv(ops):
         req.wait()
+    q[:, 0:GHOST].copy_(recv_lower)
+    q[:, nz + GHOST:].copy_(recv_upper)
 
 
 class SlabDomain:
