@@ -399,11 +399,11 @@ int32_t tgv_slab_substep(const tgv_config* cfg, const tgv_slab* slab, const void
  * device: slabs[r] must tile [0, N) in order (slabs[0].z0 = 0, each slab
  * starting where the previous ends); q[r] is slab r's state (device, slab
  * layout).  Fills every slab's four ghost planes from its periodic
- * neighbours with 20 device-to-device copies per slab (per field, the two
- * top owned planes of the slab below and the two bottom owned planes of the
- * slab above); one slab (count = 1) wraps onto itself.  Between processes
- * on different GPUs the same blocks are exchanged with point-to-point
- * messages instead (the Python binding, over NCCL).
+ * neighbours in one kernel launch (per field, the two top owned planes of the
+ * slab below and the two bottom owned planes of the slab above); one slab
+ * (count = 1) wraps onto itself.  1 <= count <= 512, else TGV_ERR_ARG.
+ * Between processes on different GPUs the same planes are exchanged with
+ * point-to-point messages instead (the Python binding, over NCCL).
  */
 int32_t tgv_slab_exchange_local(const tgv_config* cfg, int32_t count, const tgv_slab* slabs,
                                 void* const* q, void* stream);

@@ -2,6 +2,7 @@
 //
 // Host-side validation, mode dispatch, z-chunk selection and the RK3 driver
 // loop (three fused stage launches per step, buffers ping-ponged).
+#include <algorithm>
 #include <cmath>
 #include <cstring>
 #include <atomic>
@@ -173,6 +174,35 @@ static int pick_zchunk(const tgv_config& c, int tile, int occupancy, int sms, in
     if (eff > best + 1e-9) { best = eff; best_zc = zc; }
   }
   return best_zc;
+}
+
+// Ghost exchange among slabs on one device, one launch: block (x, 2c + side, r)
+// copies, for field c of slab r, either its two lower ghost planes from the two
+// top owned planes of the slab below (side 0) or its two upper ghost planes
+// from the two bottom owned planes of the slab above (side 1).  Ghost planes
+// are written and owned planes read, so no copy overlaps another.  A two-plane
+// block is 2 N^2 elements of 2, 4 or 8 bytes with N even: a whole number of
+// 32-bit words, at offsets that are multiples of 4 bytes.
+constexpr int SLAB_XCH_MAX = 512;
+struct SlabXchTable {
+  const void* q[SLAB_XCH_MAX];
+  int nz[SLAB_XCH_MAX];
+};
+
+__global__ void slab_exchange_kernel(const SlabXchTable T, int count, long long nn, int es) {
+  const int r = blockIdx.z, c = blockIdx.y >> 1, side = blockIdx.y & 1;
+  const int src_r = side ? (r + 1) % count : (r + count - 1) % count;
+  const long long fs_dst = (T.nz[r] + 4) * nn, fs_src = (T.nz[src_r] + 4) * nn;
+  const long long dst_el = c * fs_dst + (side ? (long long)(T.nz[r] + 2) * nn : 0);
+  const long long src_el = c * fs_src + (side ? 2 * nn : (long long)T.nz[src_r] * nn);
+  unsigned* dst = reinterpret_cast<unsigned*>(const_cast<char*>(static_cast<const char*>(T.q[r])) +
+                                              dst_el * es);
+  const unsigned* src =
+      reinterpret_cast<const unsigned*>(static_cast<const char*>(T.q[src_r]) + src_el * es);
+  const long long words = 2 * nn * es / 4;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < words;
+       i += (long long)gridDim.x * blockDim.x)
+    dst[i] = src[i];
 }
 
 }  // namespace tgv
@@ -602,36 +632,24 @@ int32_t tgv_slab_exchange_local(const tgv_config* cfg, int32_t count, const tgv_
                                 void* const* q, void* stream) {
   int32_t s = check(cfg);
   if (s != TGV_OK) return s;
-  if (count < 1 || !slabs || !q) return TGV_ERR_ARG;
+  if (count < 1 || count > SLAB_XCH_MAX || !slabs || !q) return TGV_ERR_ARG;
   int32_t z = 0;
+  SlabXchTable T;
   for (int32_t r = 0; r < count; ++r) {  // the slabs tile [0, N) in order
     if ((s = check_slab(cfg, &slabs[r])) != TGV_OK) return s;
     if (slabs[r].z0 != z || !q[r]) return TGV_ERR_ARG;
     z += slabs[r].nz;
+    T.q[r] = q[r];
+    T.nz[r] = slabs[r].nz;
   }
   if (z != cfg->n) return TGV_ERR_ARG;
-  const size_t es = dtype_size(cfg->q_storage);
-  const size_t nn = (size_t)cfg->n * cfg->n, blk = 2 * nn * es;
-  cudaStream_t st = (cudaStream_t)stream;
+  const int es = (int)dtype_size(cfg->q_storage);
+  const long long nn = (long long)cfg->n * cfg->n;
+  const long long words = 2 * nn * es / 4;  // one two-plane block in 32-bit words
+  const int bx = (int)std::min<long long>((words + 255) / 256, 64);
   NvtxRange range("tgv slab ghost exchange");
-  for (int32_t r = 0; r < count; ++r) {
-    const int32_t lo = (r + count - 1) % count, hi = (r + 1) % count;
-    char* dst = static_cast<char*>(q[r]);
-    const char* below = static_cast<const char*>(q[lo]);
-    const char* above = static_cast<const char*>(q[hi]);
-    const size_t fs = (size_t)slab_fs(cfg, &slabs[r]) * es;
-    const size_t fs_lo = (size_t)slab_fs(cfg, &slabs[lo]) * es;
-    const size_t fs_hi = (size_t)slab_fs(cfg, &slabs[hi]) * es;
-    for (int c = 0; c < 5; ++c) {
-      // ghosts 0-1 <- the two top owned planes of the slab below (its planes nz, nz+1)
-      TGV_CUDA_TRY(cudaMemcpyAsync(dst + c * fs, below + c * fs_lo + (size_t)slabs[lo].nz * nn * es,
-                                   blk, cudaMemcpyDeviceToDevice, st));
-      // ghosts nz+2, nz+3 <- the two bottom owned planes of the slab above (its planes 2, 3)
-      TGV_CUDA_TRY(cudaMemcpyAsync(dst + c * fs + (size_t)(slabs[r].nz + 2) * nn * es,
-                                   above + c * fs_hi + 2 * nn * es, blk,
-                                   cudaMemcpyDeviceToDevice, st));
-    }
-  }
+  slab_exchange_kernel<<<dim3(bx, 10, count), 256, 0, (cudaStream_t)stream>>>(T, count, nn, es);
+  TGV_CUDA_TRY(cudaGetLastError());
   return TGV_OK;
 }
 
