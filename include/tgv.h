@@ -352,14 +352,17 @@ int32_t tgv_run_host_stream(const tgv_config* cfg, int32_t count, const void* co
  * whole z planes of the periodic box, one per GPU, and the halos are
  * exchanged in the storage type of Q).
  *
- * tgv_slab: owned planes z0 .. z0+nz-1 of the periodic N^3 box (nz >= 2).
+ * tgv_slab: owned planes z0 .. z0+nz-1 of the N^3 box (nz >= 2).
  * Slab state layout: 5 fields, each (nz + 4) planes of N x N points, x
  * fastest: planes 0-1 are ghosts (copies of global planes z0-2, z0-1, wrapped),
  * planes 2 .. nz+1 the owned planes, planes nz+2, nz+3 ghosts (global z0+nz,
  * z0+nz+1, wrapped): element (c, k, j, i) at ((c*(nz+4) + k)*N + j)*N + i.
+ * In the symmetric box (TGV_FLAG_SYMMETRIC) the ghosts beyond a mirror face
+ * hold the raw values of the mirrored owned planes (global plane -1 <- 0,
+ * -2 <- 1, N <- N-1, N+1 <- N-2); the stage kernel applies the sign change of
+ * the normal momentum.
  * Two ghost planes match the z reach of every term of the residual.
  * A slab's Qt holds only the owned planes: ((c*nz + k)*N + j)*N + i.
- * TGV_FLAG_SYMMETRIC is not supported (TGV_ERR_UNSUPPORTED).
  */
 typedef struct tgv_slab {
   int32_t z0; /* first owned global plane */
@@ -401,7 +404,9 @@ int32_t tgv_slab_substep(const tgv_config* cfg, const tgv_slab* slab, const void
  * layout).  Fills every slab's four ghost planes from its periodic
  * neighbours in one kernel launch (per field, the two top owned planes of the
  * slab below and the two bottom owned planes of the slab above); one slab
- * (count = 1) wraps onto itself.  1 <= count <= 512, else TGV_ERR_ARG.
+ * (count = 1) wraps onto itself; in the symmetric box the first slab's lower
+ * and the last slab's upper ghosts are filled as mirror images instead (see
+ * tgv_slab).  1 <= count <= 512, else TGV_ERR_ARG.
  * Between processes on different GPUs the same planes are exchanged with
  * point-to-point messages instead (the Python binding, over NCCL).
  */

@@ -179,30 +179,41 @@ static int pick_zchunk(const tgv_config& c, int tile, int occupancy, int sms, in
 // Ghost exchange among slabs on one device, one launch: block (x, 2c + side, r)
 // copies, for field c of slab r, either its two lower ghost planes from the two
 // top owned planes of the slab below (side 0) or its two upper ghost planes
-// from the two bottom owned planes of the slab above (side 1).  Ghost planes
-// are written and owned planes read, so no copy overlaps another.  A two-plane
-// block is 2 N^2 elements of 2, 4 or 8 bytes with N even: a whole number of
-// 32-bit words, at offsets that are multiples of 4 bytes.
+// from the two bottom owned planes of the slab above (side 1).  In the
+// symmetric box the first slab's lower and the last slab's upper ghosts lie
+// beyond a mirror face instead: they take the slab's own two outermost owned
+// planes in reverse order (plane -1 <- 0, -2 <- 1; N <- N-1, N+1 <- N-2), as
+// raw values (the stage kernel applies the mirror's sign change).  Ghost
+// planes are written and owned planes read, so no copy overlaps another.  A
+// two-plane block is 2 N^2 elements of 2, 4 or 8 bytes with N even: a whole
+// number of 32-bit words, at offsets that are multiples of 4 bytes.
 constexpr int SLAB_XCH_MAX = 512;
 struct SlabXchTable {
   const void* q[SLAB_XCH_MAX];
   int nz[SLAB_XCH_MAX];
 };
 
-__global__ void slab_exchange_kernel(const SlabXchTable T, int count, long long nn, int es) {
+__global__ void slab_exchange_kernel(const SlabXchTable T, int count, long long nn, int es,
+                                     int symmetric) {
   const int r = blockIdx.z, c = blockIdx.y >> 1, side = blockIdx.y & 1;
-  const int src_r = side ? (r + 1) % count : (r + count - 1) % count;
+  const bool mirror = symmetric && (side ? r == count - 1 : r == 0);
+  const int src_r = mirror ? r : (side ? (r + 1) % count : (r + count - 1) % count);
   const long long fs_dst = (T.nz[r] + 4) * nn, fs_src = (T.nz[src_r] + 4) * nn;
   const long long dst_el = c * fs_dst + (side ? (long long)(T.nz[r] + 2) * nn : 0);
-  const long long src_el = c * fs_src + (side ? 2 * nn : (long long)T.nz[src_r] * nn);
+  // the source block: the neighbour's outermost owned planes facing this
+  // slab, or (mirror) this slab's own outermost owned planes at the face
+  const long long src_el =
+      c * fs_src + ((side != 0) != mirror ? 2 * nn : (long long)T.nz[src_r] * nn);
   unsigned* dst = reinterpret_cast<unsigned*>(const_cast<char*>(static_cast<const char*>(T.q[r])) +
                                               dst_el * es);
   const unsigned* src =
       reinterpret_cast<const unsigned*>(static_cast<const char*>(T.q[src_r]) + src_el * es);
-  const long long words = 2 * nn * es / 4;
+  const long long wpp = nn * es / 4, words = 2 * wpp;  // 32-bit words per plane, per block
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < words;
-       i += (long long)gridDim.x * blockDim.x)
-    dst[i] = src[i];
+       i += (long long)gridDim.x * blockDim.x) {
+    const long long j = mirror ? (i < wpp ? i + wpp : i - wpp) : i;  // planes swapped
+    dst[i] = src[j];
+  }
 }
 
 }  // namespace tgv
@@ -560,7 +571,6 @@ static int32_t check_slab(const tgv_config* cfg, const tgv_slab* sl) {
   int32_t s = check(cfg);
   if (s != TGV_OK) return s;
   if (!sl || sl->nz < 2 || sl->z0 < 0 || sl->z0 + sl->nz > cfg->n) return TGV_ERR_ARG;
-  if (cfg->flags & TGV_FLAG_SYMMETRIC) return TGV_ERR_UNSUPPORTED;
   return TGV_OK;
 }
 
@@ -613,6 +623,7 @@ int32_t tgv_slab_substep(const tgv_config* cfg, const tgv_slab* slab, const void
   S.bdt = RK_B[i] * dt;
   S.zg = 2;
   S.nzl = slab->nz;
+  S.zoff = slab->z0;
   S.fs_q = slab_fs(cfg, slab);
   S.fs_t = (long long)slab->nz * cfg->n * cfg->n;
   long long ctas = 0;
@@ -648,7 +659,9 @@ int32_t tgv_slab_exchange_local(const tgv_config* cfg, int32_t count, const tgv_
   const long long words = 2 * nn * es / 4;  // one two-plane block in 32-bit words
   const int bx = (int)std::min<long long>((words + 255) / 256, 64);
   NvtxRange range("tgv slab ghost exchange");
-  slab_exchange_kernel<<<dim3(bx, 10, count), 256, 0, (cudaStream_t)stream>>>(T, count, nn, es);
+  const int sym = (cfg->flags & TGV_FLAG_SYMMETRIC) ? 1 : 0;
+  slab_exchange_kernel<<<dim3(bx, 10, count), 256, 0, (cudaStream_t)stream>>>(T, count, nn, es,
+                                                                               sym);
   TGV_CUDA_TRY(cudaGetLastError());
   return TGV_OK;
 }

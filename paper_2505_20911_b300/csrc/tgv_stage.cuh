@@ -93,6 +93,10 @@ struct StageArgs {
   int zg;
   int nzl;
   long long fs_q, fs_t;
+  // A slab's global z of its first owned plane: in the symmetric box the
+  // slab's ghost planes beyond a mirror face hold the raw values of the
+  // mirrored planes, and the kernel recognises them by their global index.
+  int zoff;
 };
 
 // Ring-plane fields (compute type).  The momenta are not kept: the taps of
@@ -409,7 +413,12 @@ __device__ __forceinline__ void stage_tile(const Problem& P, const StageArgs& S,
   auto commit = [&](int slot, int zl) {  // staged raw plane -> primitives in the ring
     TC* base = ring + slot * NF * PL;
     bool fz;
-    wrap_near(zl, n, sym, &fz);
+    if (zg) {  // a slab: mirror images lie beyond the box's faces in global z
+      const int zgl = zl + S.zoff;
+      fz = sym && (zgl < 0 || zgl >= n);
+    } else {
+      wrap_near(zl, n, sym, &fz);
+    }
     const RawS* src = raw_plane(zl);
     // every unit's staged values are read before the first ring store (a
     // store may alias the staging for the compiler and hold later loads back)

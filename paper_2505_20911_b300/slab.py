@@ -38,44 +38,76 @@ def slab_bounds(n: int, world: int, rank: int) -> tuple[int, int]:
     return z0, nz
 
 
-def ghost_exchange_ops(q, rank: int, world: int, dist):
+def mirror_ghosts(q, lower: bool, upper: bool) -> None:
+    """Ghosts beyond a mirror face of the symmetric box (slab layout): the
+    slab's own two outermost owned planes in reverse order (plane -1 <- 0,
+    -2 <- 1 below; N <- N-1, N+1 <- N-2 above), raw - the stage kernel makes
+    the mirror's sign change when it reads them."""
+    nz = q.shape[1] - 2 * GHOST
+    if lower:
+        q[:, 0].copy_(q[:, 3])
+        q[:, 1].copy_(q[:, 2])
+    if upper:
+        q[:, nz + 2].copy_(q[:, nz + 1])
+        q[:, nz + 3].copy_(q[:, nz])
+
+
+def ghost_exchange_ops(q, rank: int, world: int, dist, symmetric: bool = False):
     """The point-to-point operations of one ghost exchange of a slab state q
-    ((5, nz + 4, N, N), any device), with the four buffers they use: the top
-    two owned planes of all five fields packed into one block go up, the
-    bottom two down, and one block is received from below (the lower ghosts)
-    and one from above (the upper ghosts) - four messages per rank instead of
-    one per field and direction.  The same order on every rank makes the
-    messages pair up correctly also when the two neighbours are the same rank
-    (world = 2: per peer, messages match in the order they are posted).
-    Returns (ops, recv_lower, recv_upper)."""
+    ((5, nz + 4, N, N), any device), with the buffers they use: the top two
+    owned planes of all five fields packed into one block go up, the bottom
+    two down, and one block is received from below (the lower ghosts) and one
+    from above (the upper ghosts) - four messages per rank instead of one per
+    field and direction.  In the symmetric box the first rank has no
+    neighbour below and the last none above (mirror faces): those messages
+    are left out.  The same order on every rank makes the messages pair up
+    correctly also when the two neighbours are the same rank (world = 2: per
+    peer, messages match in the order they are posted).
+    Returns (ops, recv_lower, recv_upper); a receive buffer is None where no
+    message comes."""
     import torch
     nz = q.shape[1] - 2 * GHOST
     lo, hi = (rank - 1) % world, (rank + 1) % world
-    up = q[:, nz:nz + GHOST].contiguous()
-    down = q[:, GHOST:2 * GHOST].contiguous()
-    recv_lower, recv_upper = torch.empty_like(up), torch.empty_like(down)
-    ops = [dist.P2POp(dist.isend, up, hi), dist.P2POp(dist.isend, down, lo),
-           dist.P2POp(dist.irecv, recv_lower, lo), dist.P2POp(dist.irecv, recv_upper, hi)]
+    has_lo = not (symmetric and rank == 0)
+    has_hi = not (symmetric and rank == world - 1)
+    ops, recv_lower, recv_upper = [], None, None
+    if has_hi:
+        ops.append(dist.P2POp(dist.isend, q[:, nz:nz + GHOST].contiguous(), hi))
+    if has_lo:
+        ops.append(dist.P2POp(dist.isend, q[:, GHOST:2 * GHOST].contiguous(), lo))
+        recv_lower = torch.empty_like(q[:, 0:GHOST])
+        ops.append(dist.P2POp(dist.irecv, recv_lower, lo))
+    if has_hi:
+        recv_upper = torch.empty_like(q[:, 0:GHOST])
+        ops.append(dist.P2POp(dist.irecv, recv_upper, hi))
     return ops, recv_lower, recv_upper
 
 
-def exchange_ghosts(q, rank: int, world: int, dist=None) -> None:
-    """Fill the ghost planes of this rank's slab state q from its periodic
-    neighbours (torch.distributed point-to-point: NCCL between GPUs, gloo
-    between CPU processes).  With one rank the slab is the whole periodic
-    box and its ghosts are its own wrapped planes (a local copy)."""
+def exchange_ghosts(q, rank: int, world: int, dist=None, symmetric: bool = False) -> None:
+    """Fill the ghost planes of this rank's slab state q from its neighbours
+    (torch.distributed point-to-point: NCCL between GPUs, gloo between CPU
+    processes) - periodic, or in the symmetric box mirrored at the faces.
+    With one rank the slab is the whole box and its ghosts come from its own
+    planes (a local copy)."""
     nz = q.shape[1] - 2 * GHOST
     if world == 1:
-        q[:, 0:GHOST].copy_(q[:, nz:nz + GHOST])
-        q[:, nz + GHOST:].copy_(q[:, GHOST:2 * GHOST])
+        if symmetric:
+            mirror_ghosts(q, True, True)
+        else:
+            q[:, 0:GHOST].copy_(q[:, nz:nz + GHOST])
+            q[:, nz + GHOST:].copy_(q[:, GHOST:2 * GHOST])
         return
     if dist is None:
         import torch.distributed as dist
-    ops, recv_lower, recv_upper = ghost_exchange_ops(q, rank, world, dist)
+    ops, recv_lower, recv_upper = ghost_exchange_ops(q, rank, world, dist, symmetric)
     for req in dist.batch_isend_irecv(ops):
         req.wait()
-    q[:, 0:GHOST].copy_(recv_lower)
-    q[:, nz + GHOST:].copy_(recv_upper)
+    if recv_lower is not None:
+        q[:, 0:GHOST].copy_(recv_lower)
+    if recv_upper is not None:
+        q[:, nz + GHOST:].copy_(recv_upper)
+    if symmetric:
+        mirror_ghosts(q, rank == 0, rank == world - 1)
 
 
 class SlabDomain:
@@ -127,7 +159,8 @@ class SlabDomain:
             self.tgv.tgv_slab_exchange_local(self.cfg, self.slabs,
                                              [q[self.cur] for q in self.q], stream)
         else:
-            exchange_ghosts(self.q[0][self.cur], self.rank, self.world, self.dist)
+            exchange_ghosts(self.q[0][self.cur], self.rank, self.world, self.dist,
+                            bool(self.cfg.symmetric))
 
     def step(self, dt: float, nsteps: int = 1, diag=None, stream=None) -> None:
         """nsteps RK3 steps; diag (optional device double[TGV_DIAG_COUNT]) receives

@@ -1,6 +1,6 @@
 """The z-slab decomposition's host logic (paper_2505_20911_b300.slab: the slab
-bounds and the ghost exchange over torch.distributed) on CPU ranks with the
-gloo backend, world sizes 2 and 4.  Each rank advances its slab with the FP64
+bounds and the ghost exchange over torch.distributed, periodic and in the
+symmetric box) on CPU ranks with the gloo backend, world sizes 2 and 4.  Each rank advances its slab with the FP64
 oracle on the slab plus its ghost planes; after every exchange the owned
 planes see exactly the neighbours the whole periodic box gives them, so the
 gathered slabs equal the single-domain oracle run bit for bit."""
@@ -90,3 +90,47 @@ def test_single_rank_ghosts_are_the_periodic_wrap():
     qs[:, 2:10] = q
     slab.exchange_ghosts(qs, 0, 1)
     assert torch.equal(qs[:, 0:2], q[:, 6:8]) and torch.equal(qs[:, 10:12], q[:, 0:2])
+
+
+def _mirror_worker(rank, world, port, out):
+    from paper_2505_20911_b300 import slab
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        full = torch.arange(5 * N * 3 * 2, dtype=torch.float64).reshape(5, N, 3, 2)
+        z0, nz = slab.slab_bounds(N, world, rank)
+        qs = torch.full((5, nz + 4, 3, 2), float("nan"), dtype=torch.float64)
+        qs[:, 2:2 + nz] = full[:, z0:z0 + nz]
+        slab.exchange_ghosts(qs, rank, world, dist, symmetric=True)
+        parts = [None] * world
+        dist.all_gather_object(parts, (z0, nz, qs))
+        if rank == 0:
+            out["parts"] = parts
+        dist.barrier()
+    finally:
+        dist.destroy_process_group()
+
+
+@pytest.mark.parametrize("world", [1, 2, 4])
+def test_symmetric_box_ghost_exchange(world):
+    """In the symmetric box the first rank's lower and the last rank's upper
+    ghosts are the mirror images of their own planes (global plane -1 <- 0,
+    -2 <- 1, N <- N-1, N+1 <- N-2, raw values); every inner ghost is the
+    neighbour's plane, exchanged over gloo ranks."""
+    from paper_2505_20911_b300 import slab
+    full = torch.arange(5 * N * 3 * 2, dtype=torch.float64).reshape(5, N, 3, 2)
+    # the whole box's z planes extended by its mirror images
+    ext = torch.cat([full[:, 1:2], full[:, 0:1], full, full[:, N - 1:N], full[:, N - 2:N - 1]], 1)
+    if world == 1:
+        qs = torch.full((5, N + 4, 3, 2), float("nan"), dtype=torch.float64)
+        qs[:, 2:2 + N] = full
+        slab.exchange_ghosts(qs, 0, 1, symmetric=True)
+        assert torch.equal(qs, ext)
+        return
+    port = _free_port()
+    manager = mp.get_context("spawn").Manager()
+    out = manager.dict()
+    mp.start_processes(_mirror_worker, args=(world, port, out), nprocs=world, join=True,
+                       start_method="spawn")
+    for z0, nz, qs in out["parts"]:
+        assert torch.equal(qs, ext[:, z0:z0 + nz + 4]), z0
