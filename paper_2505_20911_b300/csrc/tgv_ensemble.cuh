@@ -62,6 +62,7 @@ ensemble_stage_kernel(const EnsTable T, const double a, const double b, const in
     S.zg = 0;  // the periodic box
     S.nzl = 0;
     S.fs_q = S.fs_t = 0;
+    S.zoff = 0;
     stage_tile<TS, TT, TC, TA, TX, TY, NP, EPI_RK, false, SPL_QUAD, RKF_STAGE_ENC_RT(I)>(
         In.P, S, bx * TX, by * TY, bz * In.zchunk, 0);
     __syncthreads();  // the next item reuses the shared-memory ring

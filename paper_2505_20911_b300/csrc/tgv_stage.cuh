@@ -412,13 +412,8 @@ __device__ __forceinline__ void stage_tile(const Problem& P, const StageArgs& S,
     for (int m = 0; m < 3; ++m) qm_q[d][m] = RawS{};
   auto commit = [&](int slot, int zl) {  // staged raw plane -> primitives in the ring
     TC* base = ring + slot * NF * PL;
-    bool fz;
-    if (zg) {  // a slab: mirror images lie beyond the box's faces in global z
-      const int zgl = zl + S.zoff;
-      fz = sym && (zgl < 0 || zgl >= n);
-    } else {
-      wrap_near(zl, n, sym, &fz);
-    }
+    bool fz;  // a mirror image (symmetric box): beyond a face in global z
+    wrap_near(zl + S.zoff, n, sym, &fz);
     const RawS* src = raw_plane(zl);
     // every unit's staged values are read before the first ring store (a
     // store may alias the staging for the compiler and hold later loads back)
